@@ -1,0 +1,238 @@
+"""FP64 CPU oracle for FCFS (arXiv 2203.10670) -- TEST INFRASTRUCTURE ONLY.
+
+This package is the plain, slow reference the CUDA library is checked against.
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  The library (``paper_2203_10670_gb300``) never
+imports it, and it imports nothing from the library: the two share no code.
+
+The arithmetic lives in ``fcfs_oracle.c`` (double precision, plain loops);
+this module is argument marshalling around it with numpy float64 arrays.
+Method and padding codes (NEAREST=0, BILINEAR=1, BICUBIC=2; REPLICATE=0,
+CONSTANT=1, REFLECT=2) are the interface codes of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+NEAREST, BILINEAR, BICUBIC = 0, 1, 2
+PAD_REPLICATE, PAD_CONSTANT, PAD_REFLECT = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fcfs_oracle.c")
+_LIB = os.path.join(_HERE, "libfcfs_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP if available) into oracle/libfcfs_oracle.so."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Axis(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int), ("s", ctypes.c_int), ("method", ctypes.c_int),
+                ("K", ctypes.c_int), ("w", ctypes.POINTER(ctypes.c_double)),
+                ("w_per_channel", ctypes.c_int)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        i, ll, d = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+        P = ctypes.c_void_p
+        L.orc_kernel.restype = d
+        L.orc_kernel.argtypes = [i, d]
+        L.orc_out_len.restype = ll
+        L.orc_out_len.argtypes = [ll, i, i]
+        L.orc_kmin.argtypes = [i, i]
+        L.orc_left_offset.argtypes = [i, i]
+        L.orc_num_windows.restype = ll
+        L.orc_num_windows.argtypes = [ll, i]
+        L.orc_ext_index.restype = ll
+        L.orc_ext_index.argtypes = [ll, ll, i]
+        L.orc_make_weights.argtypes = [i, i, i, i, P]
+        for f in (L.orc_resize_direct, L.orc_resize_polyphase):
+            f.argtypes = [i, ll, ll, P, P, i, d, P, P]
+        L.orc_resize_at.argtypes = [i, i, ll, ll, P, P, i, d, P, P, ll, P]
+        L.orc_adjoint_dx.argtypes = [i, ll, ll, P, P, i, P, P]
+        L.orc_adjoint_dx_at.argtypes = [i, ll, ll, P, P, i, P, P, ll, P]
+        L.orc_weight_grad.argtypes = [i, ll, ll, P, P, i, d, P, P, P]
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+# ------------------------------------------------------------------ scalars
+
+def kernel(method: int, t: float) -> float:
+    """Interpolation kernel k(t): bilinear hat or Keys a=-0.5 cubic (Sec. 5.2)."""
+    return lib().orc_kernel(method, float(t))
+
+
+def out_len(n: int, r: int, s: int) -> int:
+    return lib().orc_out_len(n, r, s)
+
+
+def kmin(method: int, s: int) -> int:
+    return lib().orc_kmin(method, s)
+
+
+def left_offset(K: int, s: int) -> int:
+    return lib().orc_left_offset(K, s)
+
+
+def num_windows(n_out: int, r: int) -> int:
+    return lib().orc_num_windows(n_out, r)
+
+
+def ext_index(q: int, n: int, pad: int) -> int:
+    return lib().orc_ext_index(q, n, pad)
+
+
+def make_weights(method: int, r: int, s: int, K: int = 0):
+    """Dense table W[j][m] (r x (2K+1)) and the K used; K=0 means K_min."""
+    K_used = K if K else kmin(method, s)
+    W = np.zeros((r, 2 * K_used + 1), dtype=np.float64)
+    rc = lib().orc_make_weights(method, r, s, K, W.ctypes.data)
+    if rc < 0:
+        raise ValueError(f"K={K} below K_min={kmin(method, s)}")
+    return W, rc
+
+
+# ------------------------------------------------------------------ tensors
+
+def _axes(axes, keep):
+    """axes: list of dicts {r, s, method, K=0, w=None (array [C or 1][r][T] or [r][T])}."""
+    arr = (_Axis * len(axes))()
+    for k, a in enumerate(axes):
+        w = a.get("w")
+        arr[k].r, arr[k].s = a["r"], a["s"]
+        arr[k].method = a.get("method", BILINEAR)
+        arr[k].K = a.get("K", 0)
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            keep.append(w)
+            arr[k].w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[k].w_per_channel = 1 if w.ndim == 3 else 0
+            T = w.shape[-1]
+            if arr[k].K == 0:
+                arr[k].K = (T - 1) // 2
+            assert 2 * arr[k].K + 1 == T and w.shape[-2] == a["r"]
+        else:
+            arr[k].w = None
+            arr[k].w_per_channel = 0
+    return arr
+
+
+def _shapes(in_shape):
+    return (ctypes.c_longlong * 3)(*(list(in_shape) + [1] * (3 - len(in_shape))))
+
+
+def out_shape(in_shape, axes):
+    return tuple(out_len(n, a["r"], a["s"]) for n, a in zip(in_shape, axes))
+
+
+def resize(x, axes, pad=PAD_REPLICATE, pad_value=0.0, polyphase=False):
+    """y = FCFS(x).  x: float64 [n, c, *spatial]; one dict per spatial axis.
+
+    polyphase=False: fixed methods by the direct interpolation formula.
+    polyphase=True : the pad/strided-conv/pixelshuffle sum with weights w (or the
+                     method table when w is None)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, c, spatial = x.shape[0], x.shape[1], x.shape[2:]
+    nd = len(spatial)
+    assert nd == len(axes) and 1 <= nd <= 3
+    keep = []
+    ax = _axes(axes, keep)
+    y = np.empty((n, c) + out_shape(spatial, axes), dtype=np.float64)
+    if y.size == 0:
+        return y
+    f = lib().orc_resize_polyphase if polyphase else lib().orc_resize_direct
+    rc = f(nd, n, c, _shapes(spatial), ctypes.cast(ax, ctypes.c_void_p), pad, float(pad_value),
+           x.ctypes.data, y.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return y
+
+
+def resize_at(x, axes, flat_idx, pad=PAD_REPLICATE, pad_value=0.0, polyphase=False):
+    """Outputs at chosen flat indices of the [n, c, *out] result."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, c, spatial = x.shape[0], x.shape[1], x.shape[2:]
+    keep = []
+    ax = _axes(axes, keep)
+    idx = np.ascontiguousarray(flat_idx, dtype=np.int64)
+    out = np.empty(idx.shape, dtype=np.float64)
+    rc = lib().orc_resize_at(1 if polyphase else 0, len(spatial), n, c, _shapes(spatial),
+                             ctypes.cast(ax, ctypes.c_void_p), pad, float(pad_value),
+                             x.ctypes.data, idx.ctypes.data, idx.size, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def adjoint_dx(g, in_shape, axes, pad=PAD_REPLICATE):
+    """Input gradient (transposed sum with pad folding); g: [n, c, *out]."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n, c = g.shape[0], g.shape[1]
+    keep = []
+    ax = _axes(axes, keep)
+    dx = np.zeros((n, c) + tuple(in_shape), dtype=np.float64)
+    if dx.size == 0:
+        return dx
+    rc = lib().orc_adjoint_dx(len(in_shape), n, c, _shapes(in_shape), ctypes.cast(ax, ctypes.c_void_p),
+                              pad, g.ctypes.data, dx.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return dx
+
+
+def adjoint_dx_at(g, in_shape, axes, flat_idx, pad=PAD_REPLICATE):
+    """Input gradient at chosen flat indices of [n, c, *in] (gather form)."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n, c = g.shape[0], g.shape[1]
+    keep = []
+    ax = _axes(axes, keep)
+    idx = np.ascontiguousarray(flat_idx, dtype=np.int64)
+    out = np.empty(idx.shape, dtype=np.float64)
+    rc = lib().orc_adjoint_dx_at(len(in_shape), n, c, _shapes(in_shape), ctypes.cast(ax, ctypes.c_void_p),
+                                 pad, g.ctypes.data, idx.ctypes.data, idx.size, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def weight_grad(x, g, axes, pad=PAD_REPLICATE, pad_value=0.0):
+    """Per-axis weight gradients, each shaped like that axis's w ([C][r][T] or [r][T])."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n, c, spatial = x.shape[0], x.shape[1], x.shape[2:]
+    keep = []
+    ax = _axes(axes, keep)
+    outs = []
+    for k, a in enumerate(axes):
+        T = 2 * ax[k].K + 1
+        shape = (c, a["r"], T) if ax[k].w_per_channel else (a["r"], T)
+        outs.append(np.zeros(shape, dtype=np.float64))
+    ptrs = (ctypes.c_void_p * 3)(*([o.ctypes.data for o in outs] + [None] * (3 - len(outs))))
+    rc = lib().orc_weight_grad(len(spatial), n, c, _shapes(spatial), ctypes.cast(ax, ctypes.c_void_p),
+                               pad, float(pad_value), x.ctypes.data, g.ctypes.data, ptrs)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return outs
