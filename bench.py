@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""FCFS benchmark: output Gpix/s and fraction of HBM bandwidth on GB300.
+
+A step is the batched FP32 forward workload: 16x3x1080x1920 images resized by
+bicubic (Keys a=-0.5) 2/3, bicubic 4/3 and nearest 3/2 (three fused FCFS
+launches, captured in one CUDA graph).  value = output pixels (all channels of
+a pixel counted once) per second over all ranks.  Inputs (398 MB) are larger
+than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank runs its own replica of the workload (the
+layer has no exchange step); timing is the max over ranks.
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+reference arm: a deliberately slow, plain implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "output Gpix/s (fused FCFS forward, FP32, 16x3x1080x1920: bicubic 2/3 + bicubic 4/3 + nearest 3/2)"
+WORKLOAD = "c2: N=16 C=3 1080x1920 fp32 U[0,1); bicubic 2/3, bicubic 4/3, nearest 3/2; CUDA graph"
+OPS = [("bicubic_2_3", (2, 3), 2), ("bicubic_4_3", (4, 3), 2), ("nearest_3_2", (3, 2), 0)]
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASON_COLS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--no-extras", action="store_true", help="skip the BF16 / backward / large-config lines")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def out_pixels(shape, ratio):
+    n, c, h, w = shape
+    r, s = ratio
+    return n * (h * r // s) * (w * r // s)
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms in the background during a timed region."""
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            self.sel = str(device_index)
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.sel}", f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        reasons = sorted({name for r in rows for name, v in zip(REASON_COLS, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None}
+
+
+# ------------------------------------------------------------------ helpers
+
+def timed(fn, steps, stream):
+    """(seconds) of `steps` calls of fn on `stream`, CUDA events, synchronized both sides."""
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / 1e3
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2203_10670_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2203_10670_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d[kernel_key]
+        if e.get("source_hash") == kernel_source_hash():
+            return float(e["bytes_per_launch"]) * float(e.get("scale", 1.0))
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_sample(steps=1):
+    """Time the FP64 oracle on one image (3 channels) of the batch per op; returns
+    (pixels, seconds, threads, description)."""
+    import oracle
+    from paper_2203_10670_gb300 import inputs
+
+    oracle.build()
+    n, c, h, w = inputs.C2["shape"]
+    x = inputs.uniform((1, c, h, w), inputs.C2["seed"]).double().numpy()
+    pix, secs = 0, 0.0
+    for _ in range(steps):
+        for _, ratio, method in OPS:
+            t0 = time.perf_counter()
+            oracle.resize(x, [dict(r=ratio[0], s=ratio[1], method=method)] * 2)
+            secs += time.perf_counter() - t0
+            pix += out_pixels((1, c, h, w), ratio)
+    return pix, secs, oracle.num_threads(), f"1 of 16 images (3 channels, 1080x1920) per op x {steps}"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(1)
+    pix, secs, cores, sample = oracle_sample(args.steps)
+    v = pix / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Gpix/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Gpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, device):
+    from paper_2203_10670_gb300 import build as B
+
+    B.build()
+    from paper_2203_10670_gb300 import fcfs, inputs
+
+    dist = world > 1
+    stream = torch.cuda.current_stream(device)
+    shape = inputs.C2["shape"]
+    x = inputs.uniform(shape, inputs.C2["seed"], device=device)
+    axes = {name: [fcfs.Axis(r, s, m)] * 2 for name, (r, s), m in OPS}
+    outs = {name: torch.empty(fcfs.out_shape(shape, axes[name]), device=device) for name, _, _ in OPS}
+    pix_step = sum(out_pixels(shape, ratio) for _, ratio, _ in OPS)
+
+    def step():
+        for name, _, _ in OPS:
+            fcfs.resize(x, axes[name], out=outs[name])
+
+    # plan the tile shapes once (autotuner), then capture the step in a graph
+    for name, _, _ in OPS:
+        d = fcfs.make_desc(shape, axes[name], 0, 0)
+        fcfs.fcfs_tune_forward(d, x.data_ptr(), outs[name].data_ptr(), stream.cuda_stream, 3)
+    step()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            step()
+    torch.cuda.synchronize()
+
+    def replay():
+        graph.replay()
+
+    for _ in range(max(3, args.warmup)):
+        replay()
+    torch.cuda.synchronize()
+    clocks = Clocks(device.index) if rank == 0 else None
+    if dist:
+        torch.distributed.barrier()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    secs = timed(replay, args.steps, stream)
+    if clocks:
+        time.sleep(0.2)
+    clk = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([secs], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs = float(t.item())
+        torch.distributed.barrier()
+    value = world * args.steps * pix_step / secs / 1e9
+
+    # per-kernel durations (eager launches with events on the launching stream)
+    peak, peak_kind = peaks()
+    kern = {}
+    for name, ratio, _ in OPS:
+        s2 = timed(lambda n=name: fcfs.resize(x, axes[n], out=outs[n]), args.steps, stream)
+        per = s2 / args.steps
+        nbytes = x.numel() * 4 + outs[name].numel() * 4
+        kern[name] = {"ms": per * 1e3, "bytes": nbytes, "GBps": nbytes / per / 1e9,
+                      "Gpix_s": out_pixels(shape, ratio) / per / 1e9}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    dk = kern[dom]
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": dk["GBps"], "peak": peak, "unit": "GB/s", "frac": dk["GBps"] / peak,
+                "traffic": traffic, "kernel": f"fcfs_fwd2d ({dom})" if not dom.startswith("nearest") else
+                "fcfs_nearest", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": dk["bytes"]}
+
+    # end to end through the public API: pinned host input -> device -> three resizes -> pinned host outputs
+    xh = x.cpu().pin_memory()
+    outs_h = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in outs.items()}
+    xd = torch.empty_like(x)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        for name, _, _ in OPS:
+            fcfs.resize(xd, axes[name], out=outs[name])
+            outs_h[name].copy_(outs[name], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    e2e_steps = max(3, args.steps // 4)
+    es = timed(e2e_step, e2e_steps, stream)
+    if dist:
+        t = torch.tensor([es], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        es = float(t.item())
+    e2e = {"value": world * e2e_steps * pix_step / es / 1e9, "unit": "Gpix/s",
+           "h2d_bytes_per_step": x.numel() * 4, "d2h_bytes_per_step": sum(v.numel() * 4 for v in outs.values())}
+
+    line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 16 * world, "l2": "inputs larger than L2 (398 MB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "kernels": kern, "e2e": e2e, "gpu_launches": args.steps * len(OPS)}
+    if clk is not None:
+        line["clocks"] = clk
+    if rank == 0 and world == 1:
+        pix, cs, cores, sample = oracle_sample(1)
+        line["cpu_baseline"] = {"value": pix / cs / 1e9, "unit": "Gpix/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if not args.no_extras:
+        line["extras"] = extras(fcfs, inputs, device, stream, peak)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def extras(fcfs, inputs, device, stream, peak):
+    """BF16 storage of the same ops, the differentiable BF16 layer (c3) and the large configs (c5)."""
+    out = {}
+    steps = 5
+    shape = inputs.C2["shape"]
+    xb = inputs.uniform(shape, inputs.C2["seed"], device=device, dtype=torch.bfloat16)
+    for name, (r, s), m in OPS:
+        ax = [fcfs.Axis(r, s, m)] * 2
+        y = torch.empty(fcfs.out_shape(shape, ax), device=device, dtype=torch.bfloat16)
+        fcfs.resize(xb, ax, out=y)
+        t = timed(lambda: fcfs.resize(xb, ax, out=y), steps, stream) / steps
+        nb = xb.numel() * 2 + y.numel() * 2
+        out[f"bf16_{name}"] = {"ms": t * 1e3, "Gpix_s": out_pixels(shape, (r, s)) / t / 1e9,
+                               "hbm_frac": nb / t / 1e9 / peak}
+    del xb
+    # c3: 8x64x256^2 bf16, 5/4 learnable per-channel taps
+    s3 = inputs.C3["shape"]
+    W, K = fcfs.fcfs_make_weights(fcfs.BILINEAR, 5, 4)
+    wt = torch.from_numpy(np.tile(W[None], (s3[1], 1, 1))).to(device)
+    ax = [fcfs.Axis(5, 4, fcfs.BILINEAR, K, wt), fcfs.Axis(5, 4, fcfs.BILINEAR, K, wt.clone())]
+    x3 = inputs.normal(s3, inputs.C3["seed"], device=device, dtype=torch.bfloat16)
+    y3 = fcfs.resize(x3, ax)
+    g3 = inputs.normal(tuple(y3.shape), inputs.C3["grad_seed"], device=device, dtype=torch.bfloat16)
+    fcfs.resize_backward(x3, g3, ax, need_dx=True, need_dw=[True, True])
+    tf = timed(lambda: fcfs.resize(x3, ax, out=y3), steps, stream) / steps
+    tdx = timed(lambda: fcfs.resize_backward(x3, g3, ax, need_dx=True, need_dw=[False, False]), steps, stream) / steps
+    tb = timed(lambda: fcfs.resize_backward(x3, g3, ax, need_dx=True, need_dw=[True, True]), steps, stream) / steps
+    px3 = s3[0] * y3.shape[2] * y3.shape[3]
+    out["c3_bf16_fwd"] = {"ms": tf * 1e3, "Gpix_s": px3 / tf / 1e9,
+                          "hbm_frac": (x3.numel() + y3.numel()) * 2 / tf / 1e9 / peak}
+    out["c3_bf16_bwd_dx"] = {"ms": tdx * 1e3, "Gpix_s": px3 / tdx / 1e9,
+                             "hbm_frac": (x3.numel() + y3.numel()) * 2 / tdx / 1e9 / peak}
+    out["c3_bf16_bwd_dx_dw"] = {"ms": tb * 1e3, "Gpix_s": px3 / tb / 1e9,
+                                "hbm_frac": (2 * x3.numel() + y3.numel()) * 2 / tb / 1e9 / peak}
+    del x3, y3, g3
+    # c5: 1x3x8192^2 bicubic 7/5 and 256^3 trilinear 3/2, fp32 forward and input gradient
+    for key, spec, axes_n in (("c5_8192_bicubic_7_5", inputs.C5_2D, 2), ("c5_256cube_trilinear_3_2", inputs.C5_3D, 3)):
+        r, s = spec["ratio"]
+        m = fcfs.BICUBIC if axes_n == 2 else fcfs.BILINEAR
+        ax = [fcfs.Axis(r, s, m)] * axes_n
+        x5 = inputs.uniform(spec["shape"], spec["seed"], device=device)
+        y5 = fcfs.resize(x5, ax)
+        t = timed(lambda: fcfs.resize(x5, ax, out=y5), steps, stream) / steps
+        tdx = timed(lambda: fcfs.resize_backward(None, y5, ax, in_shape=tuple(x5.shape), in_dtype=x5.dtype),
+                    steps, stream) / steps
+        px = int(np.prod(y5.shape)) // y5.shape[1]
+        nb = (x5.numel() + y5.numel()) * 4
+        out[key] = {"fwd_ms": t * 1e3, "fwd_Gpix_s": px / t / 1e9, "fwd_hbm_frac": nb / t / 1e9 / peak,
+                    "bwd_dx_ms": tdx * 1e3, "bwd_dx_hbm_frac": nb / tdx / 1e9 / peak}
+        del x5, y5
+    torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+    try:
+        run_ours(args, rank, world, device)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

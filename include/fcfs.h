@@ -1,0 +1,164 @@
+/*
+ * libfcfs -- Fully Convolutional Fractional Scaling (FCFS) on GB300 (sm_103a).
+ *
+ * FCFS (Soloveitchik & Werman, arXiv 2203.10670) scales a signal by a rational
+ * factor r/s in one layer: pad the input (Sec. 3.1), apply a convolution with
+ * r output channels and stride s whose kernels are interpolation weights
+ * (Sec. 3.2), then pixel-shuffle the r channels into one output axis.  In 2D
+ * and 3D (Sec. 4) the convolution has prod(r_a) channels and a per-axis
+ * stride, followed by an N-d pixelshuffle.  This library evaluates that layer
+ * as one fused polyphase gather: the r-channel hidden layer of Sec. 3.2 is
+ * never written to memory, the pixelshuffle is the store index.
+ *
+ * Conventions used by every entry point:
+ *   - Geometry per spatial axis with input length N: output length
+ *     No = floor(N r / s); output o = i r + j (window i, phase j) samples the
+ *     input at p = o s / r (Sec. 3.2: phase j of window i interpolates at
+ *     offset i + j/r in stride units).  A window of T = 2K+1 taps starts at
+ *     input index i s - L with L = K - floor(s/2).
+ *   - Tensors are contiguous row-major [n][c][spatial...], the last spatial
+ *     axis fastest, in DEVICE memory owned by the caller.  Spatial axes are
+ *     listed outermost first: (W), (H, W) or (D, H, W).
+ *   - Weights W[j][m] multiply x~[i s - L + m] (cross-correlation order; the
+ *     true convolution of Sec. 3 is the same kernel reversed).
+ *   - Every call returns an fcfs_status; arguments are validated on the host
+ *     before anything is enqueued, and nothing is enqueued on error.  Device
+ *     work is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream); FCFS_OK means validated and enqueued.
+ *   - The library never allocates device memory on the forward/backward path.
+ */
+#ifndef FCFS_H
+#define FCFS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FCFS_OK = 0,
+    FCFS_ERR_ARG = -1,              /* malformed argument (shape, pointer, enum, size) */
+    FCFS_ERR_KERNEL_TOO_SMALL = -2, /* K below K_min for a fixed method */
+    FCFS_ERR_UNSUPPORTED = -3,      /* valid but not implemented combination */
+    FCFS_ERR_CUDA = -4,             /* a CUDA runtime call failed */
+    FCFS_ERR_NOMEM = -5,            /* workspace or serving budget too small */
+    FCFS_ERR_TIMEOUT = -6,          /* a bounded wait ran out */
+    FCFS_ERR_BUSY = -7              /* serving: no free slot right now */
+} fcfs_status;
+
+/* Interpolation methods of Sec. 5.2.  Bicubic is Keys' cubic convolution with
+ * a = -0.5 (the printed kernel's "-4a" constant is +2). */
+typedef enum { FCFS_NEAREST = 0, FCFS_BILINEAR = 1, FCFS_BICUBIC = 2 } fcfs_method;
+
+/* Padding of Sec. 3.1: repetition of edge pixels, a constant c (zeros when
+ * c = 0), and reflection about the edge sample (edge not repeated; any
+ * distance by periodic mirroring with period 2(N-1)). */
+typedef enum { FCFS_PAD_REPLICATE = 0, FCFS_PAD_CONSTANT = 1, FCFS_PAD_REFLECT = 2 } fcfs_pad;
+
+/* Sample alignment: only the paper's p = o s / r is implemented. */
+typedef enum { FCFS_ALIGN_PAPER = 0 } fcfs_align;
+
+/* Element types.  FCFS_U8 is accepted as an input type (converted exactly to
+ * FP32 at load).  Arithmetic is FP32 everywhere; BF16 is a storage format
+ * only (rounded to nearest-even on store). */
+typedef enum { FCFS_F32 = 0, FCFS_BF16 = 1, FCFS_U8 = 2 } fcfs_dtype;
+
+#define FCFS_MAX_R 64      /* largest r per axis for the built-in method tables */
+#define FCFS_MAX_TAPS 9    /* largest T = 2K+1 for learnable weights */
+
+/*
+ * Weight table of Sec. 5.2 (Sec. 3.2 "kernel_weights").  Writes the r x (2K+1)
+ * FP32 table W[j][m] = k(j s / r - (m - L)) to HOST memory w_out (row j =
+ * phase), where k is the bilinear hat or the Keys kernel; nearest is one-hot
+ * at m = floor((2 j s + r) / (2 r)) + L (round half up, the rounding the
+ * Sec. 5.2.1 examples show).  Computed in FP64, rounded once to FP32.
+ * K = 0 selects K_min = ceil((s + 2R - 2) / 2) (R = 1 nearest/bilinear,
+ * 2 bicubic); *K_out (may be NULL) receives the K used.  w_out may be NULL
+ * to query K only.  Errors: FCFS_ERR_ARG (r, s < 1, r > FCFS_MAX_R, unknown
+ * method), FCFS_ERR_KERNEL_TOO_SMALL (0 < K < K_min).
+ */
+int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out);
+
+/*
+ * Geometry of one axis (Sec. 3.2 "Description"): for input length n_in,
+ * *n_out = floor(n_in r / s), *n_windows = ceil(n_out / r), *left_offset = L.
+ * K = 0 selects K_min for `method`.  Any output pointer may be NULL.
+ */
+int fcfs_geometry(int method, int r, int s, int K, long long n_in, long long* n_out,
+                  long long* n_windows, int* left_offset);
+
+/* One spatial axis of the layer. */
+typedef struct {
+    int r, s;          /* scale factor r/s, both >= 1 (need not be reduced) */
+    int K;             /* window half width (T = 2K+1); 0 = K_min for `method` */
+    int method;        /* fcfs_method, used when w == NULL */
+    const float* w;    /* DEVICE learnable weights [C][r][T] (w_per_channel) or
+                          [r][T]; NULL = the fixed table of `method` */
+    int w_per_channel; /* 1: one table per channel (depthwise), 0: shared */
+} fcfs_axis;
+
+/* The whole layer: depthwise over channels, separable over spatial axes
+ * (Sec. 4 with outer-product kernels). */
+typedef struct {
+    int ndim;                /* spatial dimensions, 1..3 */
+    long long n, c;          /* batch and channels */
+    long long in_shape[3];   /* spatial input extents, outermost first */
+    long long out_shape[3];  /* must equal floor(in_shape * r / s) per axis */
+    int dtype_in;            /* fcfs_dtype of x (F32, BF16, U8) */
+    int dtype_out;           /* fcfs_dtype of y (F32, BF16) */
+    int pad;                 /* fcfs_pad */
+    float pad_value;         /* constant for FCFS_PAD_CONSTANT */
+    int align;               /* FCFS_ALIGN_PAPER */
+    fcfs_axis axis[3];       /* same order as in_shape */
+} fcfs_desc;
+
+/*
+ * Forward FCFS (Sec. 3.2 pseudocode; Sec. 4 for 2D/3D):
+ *   y[n,c,o] = sum_m prod_a W_a[c][j_a][m_a] x~[n,c, i_a s_a - L_a + m_a]
+ * with o_a = i_a r_a + j_a.  x: DEVICE [n][c][in_shape...] of dtype_in;
+ * y: DEVICE [n][c][out_shape...] of dtype_out, fully overwritten.  x and y
+ * must not overlap.  Nearest on every axis is an exact copy (bit-exact).
+ * Errors: FCFS_ERR_ARG, FCFS_ERR_KERNEL_TOO_SMALL, FCFS_ERR_UNSUPPORTED,
+ * FCFS_ERR_CUDA (launch failure).  Empty outputs enqueue nothing.
+ */
+int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream);
+
+/*
+ * Bytes of device workspace fcfs_backward needs for the weight gradients
+ * requested by the descriptor (0 when no axis has learnable weights).
+ */
+size_t fcfs_backward_workspace(const fcfs_desc* d);
+
+/*
+ * Backward of the forward map above (the learnable-weights remark of Sec. 6
+ * needs both gradients):
+ *   gx = adjoint of the polyphase map applied to gy, with the pad adjoint
+ *        folded in (replicate sends every virtual index to the edge pixel,
+ *        reflect to its mirror, constant drops them);
+ *   gw[a][c][j][m] = sum over n and outputs of phase j on axis a of
+ *        gy * x~ * (product of the other axes' weights).
+ * x (DEVICE, dtype_in) is needed only for gw and may be NULL otherwise;
+ * gy: DEVICE, dtype_out, shape of y; gx: DEVICE, dtype_in (F32 or BF16), shape
+ * of x, fully overwritten, may be NULL; gw: array of ndim pointers (the array
+ * itself may be NULL) to DEVICE FP32 buffers shaped like that axis's w,
+ * overwritten; gw[a] must be NULL when axis a has no learnable weights.
+ * workspace: DEVICE, at least fcfs_backward_workspace(d) bytes, 256-byte
+ * aligned, caller-owned.  Partial sums are reduced in a fixed order, so
+ * results are bitwise reproducible run to run.
+ * Errors: as fcfs_forward, plus FCFS_ERR_NOMEM when ws_bytes is too small.
+ */
+int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw,
+                  void* workspace, size_t ws_bytes, void* stream);
+
+/* Static text for a status code. */
+const char* fcfs_status_string(int status);
+
+/* Detail text of the last error returned on the calling thread ("" if none). */
+const char* fcfs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCFS_H */

@@ -1,0 +1,661 @@
+// libfcfs host side: the C ABI entry points, argument validation, the weight
+// and geometry tables of Sec. 3.2 / Sec. 5.2, and the tile planner.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <climits>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "fcfs_host.h"
+
+namespace fcfs {
+
+static thread_local std::string g_last_error;
+
+int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(FCFS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Interpolation kernels of Sec. 5.2 evaluated in FP64: the bilinear hat and
+// Keys' cubic convolution kernel with a = -1/2.
+double kernel_value(int method, double t) {
+    const double a = fabs(t);
+    if (method == FCFS_BILINEAR) return a < 1.0 ? 1.0 - a : 0.0;
+    const double ka = -0.5;
+    if (a <= 1.0) return ((ka + 2.0) * a - (ka + 3.0)) * a * a + 1.0;
+    if (a < 2.0) return ((ka * a - 5.0 * ka) * a + 8.0 * ka) * a - 4.0 * ka;
+    return 0.0;
+}
+
+int support_radius(int method) { return method == FCFS_BICUBIC ? 2 : 1; }
+
+int k_min(int method, int s) { return (s + 2 * support_radius(method) - 2 + 1) / 2; }
+
+static long long floor_div(long long a, long long b) {
+    long long q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+long long out_len(long long n, int r, int s) { return floor_div(n * (long long)r, s); }
+
+// Smallest kernel template width that holds nt taps.
+int template_taps(int nt) {
+    static const int widths[] = {1, 2, 3, 4, 5, 7, 9};
+    for (int w : widths)
+        if (w >= nt) return w;
+    return -1;
+}
+
+// Fixed-method phase table in compact form: for phase j the taps sit at
+// i*s + first_j + t relative to window i.  The sample of phase j is at
+// f_j = j s / r past i*s; the kernel is evaluated at (j s - q r) / r.
+static void fixed_phase(int method, int r, int s, int j, int* first, double* w, int* nt) {
+    const long long num = (long long)j * s;
+    const long long b = num / r;
+    if (method == FCFS_NEAREST) {
+        *first = (int)((2 * num + r) / (2LL * r));
+        w[0] = 1.0;
+        *nt = 1;
+        return;
+    }
+    const int R = support_radius(method);
+    *first = (int)(b - R + 1);
+    *nt = 2 * R;
+    for (int t = 0; t < 2 * R; ++t) {
+        const long long q = b - R + 1 + t;
+        w[t] = kernel_value(method, (double)(num - q * r) / (double)r);
+    }
+}
+
+int validate_axis(const fcfs_axis& a, int idx) {
+    if (a.r < 1 || a.s < 1) return fail(FCFS_ERR_ARG, "axis %d: r and s must be >= 1 (got %d/%d)", idx, a.r, a.s);
+    if (a.method < FCFS_NEAREST || a.method > FCFS_BICUBIC) return fail(FCFS_ERR_ARG, "axis %d: unknown method %d", idx, a.method);
+    if (a.K < 0) return fail(FCFS_ERR_ARG, "axis %d: K must be >= 0", idx);
+    if (a.w == nullptr) {
+        if (a.r > kMaxR) return fail(FCFS_ERR_ARG, "axis %d: r=%d exceeds FCFS_MAX_R=%d", idx, a.r, kMaxR);
+        if (a.K != 0 && a.K < k_min(a.method, a.s))
+            return fail(FCFS_ERR_KERNEL_TOO_SMALL, "axis %d: K=%d below K_min=%d", idx, a.K, k_min(a.method, a.s));
+    } else {
+        const int T = 2 * (a.K ? a.K : k_min(a.method, a.s)) + 1;
+        if (T > FCFS_MAX_TAPS) return fail(FCFS_ERR_UNSUPPORTED, "axis %d: %d learnable taps exceed FCFS_MAX_TAPS", idx, T);
+        if (((uintptr_t)a.w) % 4) return fail(FCFS_ERR_ARG, "axis %d: weight pointer not 4-byte aligned", idx);
+        if (a.w_per_channel != 0 && a.w_per_channel != 1) return fail(FCFS_ERR_ARG, "axis %d: w_per_channel must be 0 or 1", idx);
+    }
+    return FCFS_OK;
+}
+
+int validate_desc(const fcfs_desc* d, bool output_dtype_check) {
+    if (!d) return fail(FCFS_ERR_ARG, "descriptor is NULL");
+    if (d->ndim < 1 || d->ndim > 3) return fail(FCFS_ERR_ARG, "ndim must be 1..3 (got %d)", d->ndim);
+    if (d->n < 0 || d->c < 0) return fail(FCFS_ERR_ARG, "n and c must be >= 0");
+    if (d->dtype_in != FCFS_F32 && d->dtype_in != FCFS_BF16 && d->dtype_in != FCFS_U8)
+        return fail(FCFS_ERR_ARG, "unknown dtype_in %d", d->dtype_in);
+    if (output_dtype_check && d->dtype_out != FCFS_F32 && d->dtype_out != FCFS_BF16)
+        return fail(FCFS_ERR_ARG, "dtype_out must be F32 or BF16 (got %d)", d->dtype_out);
+    if (d->pad < FCFS_PAD_REPLICATE || d->pad > FCFS_PAD_REFLECT) return fail(FCFS_ERR_ARG, "unknown pad mode %d", d->pad);
+    if (d->align != FCFS_ALIGN_PAPER) return fail(FCFS_ERR_UNSUPPORTED, "only FCFS_ALIGN_PAPER is implemented");
+    if (d->c > INT_MAX) return fail(FCFS_ERR_ARG, "c too large");
+    for (int a = 0; a < d->ndim; ++a) {
+        int rc = validate_axis(d->axis[a], a);
+        if (rc) return rc;
+        if (d->in_shape[a] < 0 || d->in_shape[a] > INT_MAX / 2)
+            return fail(FCFS_ERR_ARG, "axis %d: input extent %lld out of range", a, d->in_shape[a]);
+        const long long no = out_len(d->in_shape[a], d->axis[a].r, d->axis[a].s);
+        if (d->out_shape[a] != no)
+            return fail(FCFS_ERR_ARG, "axis %d: out_shape %lld != floor(%lld*%d/%d) = %lld", a, d->out_shape[a],
+                        d->in_shape[a], d->axis[a].r, d->axis[a].s, no);
+        if (no > INT_MAX / 2) return fail(FCFS_ERR_ARG, "axis %d: output extent too large", a);
+    }
+    return FCFS_OK;
+}
+
+long long numel_in(const fcfs_desc* d) {
+    long long v = d->n * d->c;
+    for (int a = 0; a < d->ndim; ++a) v *= d->in_shape[a];
+    return v;
+}
+
+long long numel_out(const fcfs_desc* d) {
+    long long v = d->n * d->c;
+    for (int a = 0; a < d->ndim; ++a) v *= d->out_shape[a];
+    return v;
+}
+
+int dtype_size(int dt) { return dt == FCFS_F32 ? 4 : dt == FCFS_BF16 ? 2 : 1; }
+
+// Fill the compact polyphase form of one real axis; nt_kernel is the
+// template width every phase is evaluated with (zero-padded taps).
+void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel) {
+    memset(A, 0, sizeof(*A));
+    A->r = a.r;
+    A->s = a.s;
+    A->n_in = (int)n_in;
+    A->n_out = (int)out_len(n_in, a.r, a.s);
+    A->n_win = (int)((A->n_out + a.r - 1) / a.r);
+    A->nt = nt_kernel;
+    if (a.w) {
+        const int K = a.K ? a.K : k_min(a.method, a.s);
+        A->learn = 1;
+        A->w = a.w;
+        A->nt_src = 2 * K + 1;
+        A->w_cstride = a.w_per_channel ? (long long)a.r * A->nt_src : 0;
+        A->lo = -(K - a.s / 2);
+        A->span = nt_kernel;
+        (void)C;
+        return;
+    }
+    int first[kMaxR];
+    double w[kMaxFixedTaps];
+    int lo = INT_MAX, nt = 1;
+    for (int j = 0; j < a.r; ++j) {
+        fixed_phase(a.method, a.r, a.s, j, &first[j], w, &nt);
+        lo = std::min(lo, first[j]);
+        for (int t = 0; t < nt; ++t) A->wf[j * nt + t] = (float)w[t];
+    }
+    int span = 0;
+    for (int j = 0; j < a.r; ++j) {
+        A->off[j] = (short)(first[j] - lo);
+        span = std::max(span, first[j] - lo + nt_kernel);
+    }
+    A->nt_src = nt;
+    A->lo = lo;
+    A->span = span;
+}
+
+int axis_taps(const fcfs_axis& a) {
+    if (a.w) return 2 * (a.K ? a.K : k_min(a.method, a.s)) + 1;
+    return a.method == FCFS_NEAREST ? 1 : 2 * support_radius(a.method);
+}
+
+void identity_axis(AxisP* A, int nt_kernel) {
+    memset(A, 0, sizeof(*A));
+    A->r = A->s = 1;
+    A->n_in = A->n_out = A->n_win = 1;
+    A->nt = nt_kernel;
+    A->nt_src = 1;
+    A->wf[0] = 1.f;
+    A->span = nt_kernel;
+}
+
+// ----------------------------------------------------------- tile planning
+
+struct PlanKey {
+    int ndim, r[3], s[3], nt, din, dout;
+    bool operator==(const PlanKey& o) const { return memcmp(this, &o, sizeof(PlanKey)) == 0; }
+};
+struct PlanKeyHash {
+    size_t operator()(const PlanKey& k) const {
+        size_t h = 1469598103934665603ull;
+        const unsigned char* p = (const unsigned char*)&k;
+        for (size_t i = 0; i < sizeof(k); ++i) h = (h ^ p[i]) * 1099511628211ull;
+        return h;
+    }
+};
+static std::mutex g_plan_mu;
+static std::unordered_map<PlanKey, TileChoice, PlanKeyHash> g_plans;
+
+static PlanKey plan_key(const FwdParams& P, int ndim, int din, int dout) {
+    PlanKey k;
+    memset(&k, 0, sizeof k);
+    k.ndim = ndim;
+    for (int a = 0; a < 3; ++a) {
+        k.r[a] = P.ax[a].r;
+        k.s[a] = P.ax[a].s;
+    }
+    k.nt = P.ax[2].nt;
+    k.din = din;
+    k.dout = dout;
+    return k;
+}
+
+void set_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice t) {
+    std::lock_guard<std::mutex> g(g_plan_mu);
+    g_plans[plan_key(P, ndim, din, dout)] = t;
+}
+
+void clear_plans() {
+    std::lock_guard<std::mutex> g(g_plan_mu);
+    g_plans.clear();
+}
+
+bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t) {
+    std::lock_guard<std::mutex> g(g_plan_mu);
+    auto it = g_plans.find(plan_key(P, ndim, din, dout));
+    if (it == g_plans.end()) return false;
+    *t = it->second;
+    return true;
+}
+
+// Derive the tile sizes of P from a choice of windows per tile.
+void apply_tiles(FwdParams& P, bool is3d, int WX, int WY, int WD) {
+    const AxisP &AX = P.ax[2], &AY = P.ax[1], &AD = P.ax[0];
+    WX = std::max(1, std::min(WX, AX.n_win));
+    WY = std::max(1, std::min(WY, AY.n_win));
+    P.WX = WX;
+    P.WY = WY;
+    P.OX = WX * AX.r;
+    P.OY = WY * AY.r;
+    P.IC = (WX - 1) * AX.s + AX.span;
+    P.ICp = P.IC;
+    P.IR = (WY - 1) * AY.s + AY.span;
+    int G = std::max(1, (256 + P.OX / 2) / P.OX);
+    while (P.OX * G > 512 && G > 1) --G;
+    P.G = G;
+    P.tiles_x = (AX.n_win + WX - 1) / WX;
+    P.tiles_y = (AY.n_win + WY - 1) / WY;
+    if (is3d) {
+        WD = std::max(1, std::min(WD, AD.n_win));
+        P.WD = WD;
+        P.tiles_d = (AD.n_win + WD - 1) / WD;
+        P.ring = AD.span;
+    } else {
+        P.WD = 1;
+        P.tiles_d = 1;
+        P.ring = 0;
+    }
+}
+
+// Heuristic tile: about 128 output columns, as many rows as fit the
+// shared-memory budget (several CTAs per SM), depth chunks for enough CTAs.
+TileChoice default_tiles(const FwdParams& P0, bool is3d) {
+    FwdParams P = P0;
+    const AxisP &AX = P.ax[2], &AY = P.ax[1], &AD = P.ax[0];
+    int WX = std::max(1, 128 / AX.r);
+    int WY = std::max(1, (is3d ? 24 : 48) / AY.r);
+    const size_t budget = 60 * 1024;
+    for (int it = 0; it < 64; ++it) {
+        apply_tiles(P, is3d, WX, WY, 1);
+        if (forward_smem_bytes(P, is3d) <= budget) break;
+        if (WY > 1 && (P.IR >= P.IC / 2 || WX == 1)) WY = (WY + 1) / 2;
+        else if (WX > 1) WX = (WX + 1) / 2;
+        else break;
+    }
+    int WD = 1;
+    if (is3d) {
+        const long long base = (long long)P.tiles_x * P.tiles_y * P.planes;
+        const long long want = 152LL * 6;
+        const long long chunks = std::max(1LL, (want + base - 1) / base);
+        WD = (int)std::max(1LL, (AD.n_win + chunks - 1) / chunks);
+    }
+    return TileChoice{WX, WY, WD};
+}
+
+}  // namespace fcfs
+
+using namespace fcfs;
+
+extern "C" {
+
+const char* fcfs_status_string(int status) {
+    switch (status) {
+        case FCFS_OK: return "ok";
+        case FCFS_ERR_ARG: return "invalid argument";
+        case FCFS_ERR_KERNEL_TOO_SMALL: return "kernel half width K below K_min";
+        case FCFS_ERR_UNSUPPORTED: return "unsupported combination";
+        case FCFS_ERR_CUDA: return "CUDA error";
+        case FCFS_ERR_NOMEM: return "insufficient memory or workspace";
+        case FCFS_ERR_TIMEOUT: return "timed out";
+        case FCFS_ERR_BUSY: return "busy";
+        default: return "unknown status";
+    }
+}
+
+const char* fcfs_last_error(void) { return g_last_error.c_str(); }
+
+int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out) {
+    clear_error();
+    if (r < 1 || s < 1 || r > kMaxR) return fail(FCFS_ERR_ARG, "r, s must be >= 1 and r <= %d", kMaxR);
+    if (method < FCFS_NEAREST || method > FCFS_BICUBIC) return fail(FCFS_ERR_ARG, "unknown method %d", method);
+    const int km = k_min(method, s);
+    if (K < 0) return fail(FCFS_ERR_ARG, "K must be >= 0");
+    if (K == 0) K = km;
+    if (K < km) return fail(FCFS_ERR_KERNEL_TOO_SMALL, "K=%d below K_min=%d", K, km);
+    if (K_out) *K_out = K;
+    if (!w_out) return FCFS_OK;
+    const int T = 2 * K + 1, L = K - s / 2;
+    for (int j = 0; j < r; ++j) {
+        int first, nt;
+        double w[kMaxFixedTaps];
+        fixed_phase(method, r, s, j, &first, w, &nt);
+        for (int m = 0; m < T; ++m) w_out[j * T + m] = 0.f;
+        for (int t = 0; t < nt; ++t) {
+            const int m = first + t + L;  // tap offset first+t from i*s, window origin i*s - L
+            if (m >= 0 && m < T) w_out[j * T + m] = (float)w[t];
+        }
+    }
+    return FCFS_OK;
+}
+
+int fcfs_geometry(int method, int r, int s, int K, long long n_in, long long* n_out, long long* n_windows,
+                  int* left_offset) {
+    clear_error();
+    if (r < 1 || s < 1) return fail(FCFS_ERR_ARG, "r and s must be >= 1");
+    if (method < FCFS_NEAREST || method > FCFS_BICUBIC) return fail(FCFS_ERR_ARG, "unknown method %d", method);
+    if (n_in < 0) return fail(FCFS_ERR_ARG, "n_in must be >= 0");
+    if (K == 0) K = k_min(method, s);
+    const long long no = out_len(n_in, r, s);
+    if (n_out) *n_out = no;
+    if (n_windows) *n_windows = (no + r - 1) / r;
+    if (left_offset) *left_offset = K - s / 2;
+    return FCFS_OK;
+}
+
+int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
+    clear_error();
+    int rc = validate_desc(d, true);
+    if (rc) return rc;
+    if (numel_out(d) == 0) return FCFS_OK;
+    if (!x || !y) return fail(FCFS_ERR_ARG, "x and y must be device pointers");
+    if (((uintptr_t)x) % dtype_size(d->dtype_in) || ((uintptr_t)y) % dtype_size(d->dtype_out))
+        return fail(FCFS_ERR_ARG, "x or y not aligned to its element size");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    bool all_nearest = true;
+    for (int a = 0; a < d->ndim; ++a) all_nearest &= (d->axis[a].w == nullptr && d->axis[a].method == FCFS_NEAREST);
+    if (all_nearest) {
+        NearestParams P;
+        memset(&P, 0, sizeof P);
+        const int lead = 3 - d->ndim;
+        for (int a = 0; a < 3; ++a) {
+            if (a < lead) {
+                P.r[a] = P.s[a] = P.n_in[a] = P.n_out[a] = 1;
+            } else {
+                P.r[a] = d->axis[a - lead].r;
+                P.s[a] = d->axis[a - lead].s;
+                P.n_in[a] = (int)d->in_shape[a - lead];
+                P.n_out[a] = (int)d->out_shape[a - lead];
+            }
+        }
+        P.planes = d->n * d->c;
+        P.pad = d->pad;
+        P.padv = d->pad_value;
+        P.OXT = P.n_out[2] >= 256 ? 256 : P.n_out[2] > 64 ? 128 : P.n_out[2] > 32 ? 64 : 32;
+        P.OYT = std::min(64, 2048 / P.OXT);
+        P.tiles_x = (P.n_out[2] + P.OXT - 1) / P.OXT;
+        P.tiles_y = (P.n_out[1] + P.OYT - 1) / P.OYT;
+        P.x = x;
+        P.y = y;
+        if ((long long)P.tiles_x * P.tiles_y * P.n_out[0] * P.planes > INT_MAX)
+            return fail(FCFS_ERR_UNSUPPORTED, "grid too large");
+        cudaError_t e = launch_nearest(P, d->dtype_in, d->dtype_out, st);
+        return e == cudaSuccess ? FCFS_OK : cuda_fail(e, "nearest launch");
+    }
+
+    FwdParams P;
+    int ntk;
+    rc = build_forward_params(d, x, y, &P, &ntk);
+    if (rc) return rc;
+    const bool is3d = d->ndim == 3;
+    TileChoice tc;
+    if (!get_plan(P, d->ndim, d->dtype_in, d->dtype_out, &tc)) tc = default_tiles(P, is3d);
+    apply_tiles(P, is3d, tc.WX, tc.WY, tc.WD);
+    return launch_planned(P, ntk, is3d, d->dtype_in, d->dtype_out, st);
+}
+
+}  // extern "C"
+
+namespace fcfs {
+
+int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* out, int* ntk) {
+    int nt = 1;
+    for (int a = 0; a < d->ndim; ++a) nt = std::max(nt, axis_taps(d->axis[a]));
+    const int w = template_taps(nt);
+    if (w < 0) return fail(FCFS_ERR_UNSUPPORTED, "%d taps per phase exceed the kernel templates", nt);
+    FwdParams& P = *out;
+    memset(&P, 0, sizeof P);
+    const int lead = 3 - d->ndim;
+    for (int a = 0; a < 3; ++a) {
+        if (a < lead) identity_axis(&P.ax[a], w);
+        else fill_axis(&P.ax[a], d->axis[a - lead], d->in_shape[a - lead], (int)d->c, w);
+    }
+    P.planes = d->n * d->c;
+    P.C = (int)d->c;
+    P.pad = d->pad;
+    P.padv = d->pad_value;
+    P.x = x;
+    P.y = y;
+    *ntk = w;
+    return FCFS_OK;
+}
+
+int launch_planned(FwdParams& P, int ntk, bool is3d, int din, int dout, cudaStream_t st) {
+    const size_t smem = forward_smem_bytes(P, is3d);
+    if (smem > 227 * 1024) return fail(FCFS_ERR_UNSUPPORTED, "tile needs %zu bytes of shared memory", smem);
+    const long long blocks = (long long)P.tiles_x * P.tiles_y * P.tiles_d * P.planes;
+    if (blocks > INT_MAX) return fail(FCFS_ERR_UNSUPPORTED, "grid too large");
+    cudaError_t e = is3d ? launch_forward_3d(P, ntk, din, dout, st) : launch_forward_2d(P, ntk, din, dout, st);
+    return e == cudaSuccess ? FCFS_OK : cuda_fail(e, "forward launch");
+}
+
+}  // namespace fcfs
+
+// ---------------------------------------------------------------- backward
+
+namespace fcfs {
+
+// Transposed tap table of one axis (see AdjAxis): entry (k, j, t) of residue u
+// for every tap with relative offset e = off[j] + t = u + k*s.
+int build_adjoint(const AxisP& A, AdjAxis* J) {
+    memset(J, 0, sizeof(*J));
+    if (A.s > kMaxS) return fail(FCFS_ERR_UNSUPPORTED, "backward supports s <= %d", kMaxS);
+    if (A.r * A.nt_src > kMaxAdj) return fail(FCFS_ERR_UNSUPPORTED, "backward table too large");
+    int count[kMaxS] = {0};
+    int emax = 0;
+    for (int j = 0; j < A.r; ++j)
+        for (int t = 0; t < A.nt_src; ++t) {
+            const int e = A.off[j] + t;
+            count[e % A.s]++;
+            emax = std::max(emax, e);
+        }
+    J->ustart[0] = 0;
+    for (int u = 0; u < A.s; ++u) J->ustart[u + 1] = J->ustart[u] + count[u];
+    int fillp[kMaxS];
+    for (int u = 0; u < A.s; ++u) fillp[u] = J->ustart[u];
+    for (int j = 0; j < A.r; ++j)
+        for (int t = 0; t < A.nt_src; ++t) {
+            const int e = A.off[j] + t;
+            const int u = e % A.s, k = e / A.s;
+            J->ent[fillp[u]++] = (k << 16) | (j << 8) | t;
+        }
+    J->vmin = A.lo;
+    J->vmax = (A.n_win - 1) * A.s + A.lo + emax;
+    return FCFS_OK;
+}
+
+// Largest g extent (windows * r) any input tile of width Q needs on one axis.
+static int g_capacity(const AxisP& A, const AdjAxis& J, int pad, int Q) {
+    int cap = 0;
+    for (int q0 = 0; q0 < A.n_in; q0 += Q) {
+        const int q1 = std::min(A.n_in, q0 + Q) - 1;
+        const WinRange w = win_range(A, J, pad, q0, q1);
+        cap = std::max(cap, (w.ihi - w.ilo + 1) * A.r);
+    }
+    return std::max(cap, 1);
+}
+
+int build_backward_params(const fcfs_desc* d, const void* x, const void* gy, void* gx, BwdParams* out, int* ntk) {
+    BwdParams& B = *out;
+    memset(&B, 0, sizeof B);
+    int rc = build_forward_params(d, x, nullptr, &B.fw, ntk);
+    if (rc) return rc;
+    for (int a = 0; a < 3; ++a) {
+        B.ax[a] = B.fw.ax[a];
+        rc = build_adjoint(B.ax[a], &B.adj[a]);
+        if (rc) return rc;
+    }
+    B.planes = B.fw.planes;
+    B.C = B.fw.C;
+    B.pad = d->pad;
+    B.padv = d->pad_value;
+    B.x = x;
+    B.gy = gy;
+    B.gx = gx;
+    B.n = d->n;
+    return FCFS_OK;
+}
+
+void plan_dx(BwdParams& B, bool is3d) {
+    const AxisP &AX = B.ax[2], &AY = B.ax[1], &AD = B.ax[0];
+    B.QX = AX.n_in >= 128 ? 128 : AX.n_in > 64 ? 128 : AX.n_in > 32 ? 64 : 32;
+    B.QY = is3d ? 16 : 32;
+    if (is3d && B.QX > 64) B.QX = 64;
+    B.QY = std::min(B.QY, std::max(1, AY.n_in));
+    B.Gq = std::max(1, 256 / B.QX);
+    for (int it = 0; it < 16; ++it) {
+        B.GCcap = g_capacity(AX, B.adj[2], B.pad, B.QX);
+        B.GRcap = g_capacity(AY, B.adj[1], B.pad, B.QY);
+        B.GCp = B.GCcap;
+        B.GDcap = is3d ? g_capacity(AD, B.adj[0], B.pad, 1) : 1;
+        if (dx_smem_bytes(B, is3d) <= 100 * 1024 || (B.QY == 1 && B.QX == 32)) break;
+        if (B.QY > 1) B.QY = (B.QY + 1) / 2;
+        else B.QX = std::max(32, B.QX / 2);
+    }
+    B.qtiles_x = (AX.n_in + B.QX - 1) / B.QX;
+    B.qtiles_y = (AY.n_in + B.QY - 1) / B.QY;
+    if (is3d) {
+        const long long base = (long long)B.qtiles_x * B.qtiles_y * B.planes;
+        const long long chunks = std::max(1LL, (152LL * 6 + base - 1) / base);
+        B.QD = (int)std::max(1LL, (AD.n_in + chunks - 1) / chunks);
+        B.qtiles_d = (AD.n_in + B.QD - 1) / B.QD;
+    } else {
+        B.QD = 1;
+        B.qtiles_d = 1;
+    }
+}
+
+void plan_dw(BwdParams& B) {
+    FwdParams& P = B.fw;
+    int WX = std::max(1, 128 / P.ax[2].r);
+    int WY = std::max(1, 32 / P.ax[1].r);
+    for (int it = 0; it < 64; ++it) {
+        apply_tiles(P, false, WX, WY, 1);
+        if (dw_smem_bytes(B) <= 110 * 1024) break;
+        if (WY > 1) WY = (WY + 1) / 2;
+        else if (WX > 1) WX = (WX + 1) / 2;
+        else break;
+    }
+    const int nt = P.ax[2].nt;
+    B.dw_axis_off[0] = 0;
+    B.dw_axis_off[1] = 0;
+    B.dw_axis_off[2] = P.ax[1].r * nt;
+    B.dw_rec = (P.ax[1].r + P.ax[2].r) * nt;
+}
+
+static size_t dw_workspace(const BwdParams& B) {
+    const long long recs = (long long)B.fw.tiles_x * B.fw.tiles_y * B.planes;
+    return (size_t)(((recs * B.dw_rec * sizeof(float)) + 255) / 256 * 256);
+}
+
+static bool any_learnable(const fcfs_desc* d) {
+    for (int a = 0; a < d->ndim; ++a)
+        if (d->axis[a].w) return true;
+    return false;
+}
+
+}  // namespace fcfs
+
+extern "C" {
+
+size_t fcfs_backward_workspace(const fcfs_desc* d) {
+    clear_error();
+    if (validate_desc(d, true) != FCFS_OK) return 0;
+    if (!any_learnable(d) || d->ndim == 3 || numel_out(d) == 0) return 0;
+    BwdParams B;
+    int ntk;
+    if (build_backward_params(d, nullptr, nullptr, nullptr, &B, &ntk) != FCFS_OK) return 0;
+    plan_dw(B);
+    return dw_workspace(B);
+}
+
+int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw, void* workspace,
+                  size_t ws_bytes, void* stream) {
+    clear_error();
+    int rc = validate_desc(d, true);
+    if (rc) return rc;
+    if (d->dtype_in == FCFS_U8) return fail(FCFS_ERR_UNSUPPORTED, "no gradient for uint8 inputs");
+    bool want_w = false;
+    for (int a = 0; a < d->ndim && gw; ++a) {
+        if (!gw[a]) continue;
+        if (!d->axis[a].w) return fail(FCFS_ERR_ARG, "gw[%d] given but axis %d has no learnable weights", a, a);
+        if (((uintptr_t)gw[a]) % 4) return fail(FCFS_ERR_ARG, "gw[%d] not 4-byte aligned", a);
+        want_w = true;
+    }
+    if (want_w && d->ndim == 3) return fail(FCFS_ERR_UNSUPPORTED, "weight gradients are implemented for 1D/2D");
+    if (!gx && !want_w) return FCFS_OK;
+    if (numel_in(d) == 0) return FCFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool empty_out = numel_out(d) == 0;
+    if (!empty_out && !gy) return fail(FCFS_ERR_ARG, "gy is NULL");
+    if (gy && ((uintptr_t)gy) % dtype_size(d->dtype_out)) return fail(FCFS_ERR_ARG, "gy misaligned");
+    if (gx && ((uintptr_t)gx) % dtype_size(d->dtype_in)) return fail(FCFS_ERR_ARG, "gx misaligned");
+    if (empty_out) {
+        // no output depends on x: the gradients are zero
+        if (gx) {
+            cudaError_t e = cudaMemsetAsync(gx, 0, (size_t)numel_in(d) * dtype_size(d->dtype_in), st);
+            if (e != cudaSuccess) return cuda_fail(e, "memset gx");
+        }
+        for (int a = 0; a < d->ndim && gw; ++a) {
+            if (!gw[a]) continue;
+            const int K = d->axis[a].K ? d->axis[a].K : k_min(d->axis[a].method, d->axis[a].s);
+            const size_t n = (size_t)(d->axis[a].w_per_channel ? d->c : 1) * d->axis[a].r * (2 * K + 1);
+            cudaError_t e = cudaMemsetAsync(gw[a], 0, n * sizeof(float), st);
+            if (e != cudaSuccess) return cuda_fail(e, "memset gw");
+        }
+        return FCFS_OK;
+    }
+    BwdParams B;
+    int ntk;
+    rc = build_backward_params(d, x, gy, gx, &B, &ntk);
+    if (rc) return rc;
+    const bool is3d = d->ndim == 3;
+    if (want_w) {
+        if (!x) return fail(FCFS_ERR_ARG, "x is required for weight gradients");
+        if (((uintptr_t)x) % dtype_size(d->dtype_in)) return fail(FCFS_ERR_ARG, "x misaligned");
+        plan_dw(B);
+        const size_t need = dw_workspace(B);
+        if (!workspace || ws_bytes < need)
+            return fail(FCFS_ERR_NOMEM, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+        if (((uintptr_t)workspace) % 256) return fail(FCFS_ERR_ARG, "workspace not 256-byte aligned");
+        B.ws = (float*)workspace;
+        const int lead = 3 - d->ndim;
+        for (int a = 0; a < d->ndim; ++a) B.gw[lead + a] = gw[a];
+        const long long blocks = (long long)B.fw.tiles_x * B.fw.tiles_y * B.planes;
+        if (blocks > INT_MAX || dw_smem_bytes(B) > 227 * 1024) return fail(FCFS_ERR_UNSUPPORTED, "weight-gradient tile too large");
+    }
+    if (gx) {
+        plan_dx(B, is3d);
+        if (is3d && B.GDcap > 256) return fail(FCFS_ERR_UNSUPPORTED, "depth ratio needs more than 256 gradient planes per tile");
+        const long long blocks = (long long)B.qtiles_x * B.qtiles_y * B.qtiles_d * B.planes;
+        if (blocks > INT_MAX || dx_smem_bytes(B, is3d) > 227 * 1024)
+            return fail(FCFS_ERR_UNSUPPORTED, "input-gradient tile too large");
+        cudaError_t e = launch_dx(B, ntk, d->dtype_out, d->dtype_in, is3d, st);
+        if (e != cudaSuccess) return cuda_fail(e, "input-gradient launch");
+    }
+    if (want_w) {
+        cudaError_t e = launch_dw(B, ntk, d->dtype_in, d->dtype_out, st);
+        if (e != cudaSuccess) return cuda_fail(e, "weight-gradient launch");
+        e = launch_dw_reduce(B, st);
+        if (e != cudaSuccess) return cuda_fail(e, "weight-gradient reduce launch");
+    }
+    return FCFS_OK;
+}
+
+}  // extern "C"

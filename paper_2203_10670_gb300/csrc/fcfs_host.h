@@ -1,0 +1,43 @@
+// Host-side helpers shared by the libfcfs translation units.
+#pragma once
+
+#include <stdarg.h>
+
+#include "fcfs_internal.cuh"
+
+namespace fcfs {
+
+struct TileChoice {
+    int WX, WY, WD;  // windows per tile along x, y, depth
+};
+
+int fail(int status, const char* fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char* what);
+
+double kernel_value(int method, double t);
+int support_radius(int method);
+int k_min(int method, int s);
+long long out_len(long long n, int r, int s);
+int template_taps(int nt);
+int axis_taps(const fcfs_axis& a);
+
+int validate_axis(const fcfs_axis& a, int idx);
+int validate_desc(const fcfs_desc* d, bool output_dtype_check);
+long long numel_in(const fcfs_desc* d);
+long long numel_out(const fcfs_desc* d);
+int dtype_size(int dt);
+
+void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel);
+void identity_axis(AxisP* A, int nt_kernel);
+
+int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* out, int* ntk);
+void apply_tiles(FwdParams& P, bool is3d, int WX, int WY, int WD);
+TileChoice default_tiles(const FwdParams& P, bool is3d);
+void set_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice t);
+void clear_plans();
+bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t);
+int launch_planned(FwdParams& P, int ntk, bool is3d, int din, int dout, cudaStream_t st);
+int build_adjoint(const AxisP& A, AdjAxis* J);
+
+}  // namespace fcfs

@@ -1,0 +1,167 @@
+// Internal definitions shared by the libfcfs translation units: launch
+// parameter blocks, per-axis polyphase tables and small device helpers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fcfs.h"
+
+namespace fcfs {
+
+constexpr int kMaxR = FCFS_MAX_R;   // phases per axis in the fixed tables
+constexpr int kMaxFixedTaps = 4;    // nearest 1, bilinear 2, bicubic 4
+
+// One spatial axis in compact polyphase form.  Window i reads the input
+// positions [i*s + lo, i*s + lo + span); phase j uses the nt taps starting at
+// i*s + lo + off[j].  Learnable weights are dense (off[j] = 0, nt = T,
+// lo = -L); the fixed methods keep only the taps inside the kernel support.
+struct AxisP {
+    int r, s;
+    int lo;        // first input offset of a window relative to i*s
+    int span;      // input positions one window reads (with taps padded to nt)
+    int nt;        // taps per phase as the kernel evaluates them (template width)
+    int nt_src;    // taps per phase stored in the table (<= nt; the rest are zero)
+    int n_in, n_out, n_win;
+    int learn;               // 1: weights from the device pointer w
+    const float* w;          // learnable [C or 1][r][nt_src]
+    long long w_cstride;     // floats between channels (0 = shared)
+    short off[kMaxR];        // per-phase first tap relative to lo
+    float wf[kMaxR * kMaxFixedTaps];  // fixed-method table [r][nt_src]
+};
+
+// Forward launch parameters.  Axis 0 = D, 1 = H (y), 2 = W (x); missing axes
+// are identity axes of extent 1.
+struct FwdParams {
+    AxisP ax[3];
+    long long planes;  // n * c
+    int C;
+    int pad;
+    float padv;
+    // tile shape (windows per tile) and derived sizes
+    int WX, WY, WD;
+    int OX, OY;        // outputs per tile row/column: WX*r_x, WY*r_y
+    int IC, ICp, IR;   // input tile columns (pitch) and rows
+    int G;             // thread groups: blockDim.x = OX * G
+    int tiles_x, tiles_y, tiles_d;
+    int ring;          // 3D: depth planes kept in shared memory
+    const void* x;
+    void* y;
+};
+
+// Adjoint (transposed) polyphase table of one axis.  With v an extended
+// input index and v - lo = a*s + u (0 <= u < s), the forward taps reaching v
+// are the entries (k, j, t) of residue u: window i = a - k, phase j, tap t.
+// Every (j, t) appears once, so there are r*nt entries in total.
+constexpr int kMaxS = 64;
+constexpr int kMaxAdj = kMaxR * 9;
+struct AdjAxis {
+    int ustart[kMaxS + 1];
+    int ent[kMaxAdj];  // k << 16 | j << 8 | t
+    int vmin, vmax;    // extended indices any window touches
+};
+
+// Backward launch parameters.  The input-gradient kernels tile the INPUT
+// (real indices q); the weight-gradient kernel tiles the OUTPUT like the
+// forward.
+struct BwdParams {
+    AxisP ax[3];
+    AdjAxis adj[3];
+    long long planes;
+    int C;
+    int pad;
+    float padv;
+    // input-gradient tiling
+    int QX, QY, QD;          // real input indices per tile
+    int qtiles_x, qtiles_y, qtiles_d;
+    int GRcap, GCcap, GDcap; // g tile capacity (rows, cols, depth planes)
+    int GCp;                 // g tile pitch
+    int Gq;                  // thread groups: blockDim = QX * Gq
+    // weight-gradient tiling (output tiles as the forward)
+    FwdParams fw;
+    int dw_axis_off[3];      // offset of each axis's partials in a CTA record (floats)
+    int dw_rec;              // floats per CTA record
+    const void* x;
+    const void* gy;
+    void* gx;
+    float* ws;
+    float* gw[3];
+    long long n;
+};
+
+struct NearestParams {
+    int r[3], s[3], n_in[3], n_out[3];
+    long long planes;
+    int pad;
+    float padv;
+    int OXT, OYT;  // outputs per block along x and y
+    int tiles_x, tiles_y;
+    const void* x;
+    void* y;
+};
+
+__host__ __device__ inline int ext_index(int q, int n, int pad) {
+    if ((unsigned)q < (unsigned)n) return q;
+    if (pad == FCFS_PAD_CONSTANT) return -1;
+    if (pad == FCFS_PAD_REPLICATE) return q < 0 ? 0 : n - 1;
+    if (n == 1) return 0;
+    int p = 2 * (n - 1);
+    int m = q % p;
+    if (m < 0) m += p;
+    return m < n ? m : p - m;
+}
+
+__device__ __forceinline__ float load_f(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float load_f(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p)));
+}
+__device__ __forceinline__ float load_f(const uint8_t* p) { return (float)__ldg(p); }
+
+__device__ __forceinline__ void store_f(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_f(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+__host__ __device__ inline int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
+
+// Window range [ilo, ihi] of one axis whose taps reach the extended indices
+// that fold onto real indices [q0, q1] (inclusive), and whether the tile
+// takes the virtual indices left of 0 / right of N-1.
+struct WinRange {
+    int ilo, ihi, left, right;
+};
+
+__host__ __device__ inline WinRange win_range(const AxisP& A, const AdjAxis& J, int pad, int q0, int q1) {
+    WinRange w;
+    const int N = A.n_in;
+    w.left = pad != FCFS_PAD_CONSTANT && J.vmin < 0 && q0 <= -J.vmin;
+    const int rlim = imin(N - 1, 2 * (N - 1) - J.vmax);
+    w.right = pad != FCFS_PAD_CONSTANT && J.vmax > N - 1 && q1 >= rlim;
+    int vlo = w.left ? J.vmin : q0;
+    int vhi = w.right ? J.vmax : q1;
+    vlo = imax(vlo, J.vmin);
+    vhi = imin(vhi, J.vmax);
+    if (vlo > vhi) {
+        w.ilo = 0;
+        w.ihi = -1;
+        return w;
+    }
+    const int a = vlo - A.lo - A.span + 1;
+    w.ilo = imax(0, a >= 0 ? (a + A.s - 1) / A.s : -((-a) / A.s));
+    const int b = vhi - A.lo;
+    w.ihi = imin(A.n_win - 1, b >= 0 ? b / A.s : -((-b + A.s - 1) / A.s));
+    return w;
+}
+
+// host-side launchers (fcfs_fwd.cu / fcfs_bwd.cu)
+cudaError_t launch_forward_2d(const FwdParams& P, int nt, int din, int dout, cudaStream_t st);
+cudaError_t launch_forward_3d(const FwdParams& P, int nt, int din, int dout, cudaStream_t st);
+cudaError_t launch_nearest(const NearestParams& P, int din, int dout, cudaStream_t st);
+size_t forward_smem_bytes(const FwdParams& P, bool is3d);
+size_t dx_smem_bytes(const BwdParams& P, bool is3d);
+size_t dw_smem_bytes(const BwdParams& P);
+cudaError_t launch_dx(const BwdParams& P, int nt, int dg, int dx, bool is3d, cudaStream_t st);
+cudaError_t launch_dw(const BwdParams& P, int nt, int din, int dg, cudaStream_t st);
+cudaError_t launch_dw_reduce(const BwdParams& P, cudaStream_t st);
+
+}  // namespace fcfs

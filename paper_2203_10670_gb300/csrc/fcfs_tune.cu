@@ -1,0 +1,83 @@
+// Tile-shape autotuner: times a small candidate set of forward tile shapes
+// for one (method, r, s, dtype, ndim) key on the caller's buffers and keeps
+// the fastest in the process-wide plan cache that fcfs_forward consults.
+#include <climits>
+#include <vector>
+
+#include "fcfs_host.h"
+
+using namespace fcfs;
+
+extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, void* stream, int reps, float* best_ms,
+                                 int* n_candidates) {
+    clear_error();
+    int rc = validate_desc(d, true);
+    if (rc) return rc;
+    if (reps < 1) reps = 3;
+    if (best_ms) *best_ms = 0.f;
+    if (n_candidates) *n_candidates = 0;
+    if (numel_out(d) == 0) return FCFS_OK;
+    if (!x || !y) return fail(FCFS_ERR_ARG, "x and y must be device pointers");
+    bool all_nearest = true;
+    for (int a = 0; a < d->ndim; ++a) all_nearest &= (d->axis[a].w == nullptr && d->axis[a].method == FCFS_NEAREST);
+    if (all_nearest) return FCFS_OK;  // the nearest copy kernel has no tile choice
+    cudaStreamCaptureStatus cs;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(FCFS_ERR_ARG, "tuning cannot run during stream capture");
+
+    FwdParams P0;
+    int ntk;
+    rc = build_forward_params(d, x, y, &P0, &ntk);
+    if (rc) return rc;
+    const bool is3d = d->ndim == 3;
+    const TileChoice def = default_tiles(P0, is3d);
+    std::vector<TileChoice> cands = {def};
+    const int ox_targets[] = {64, 128, 256};
+    const int oy_targets[] = {8, 16, 32, 64};
+    for (int oxt : ox_targets)
+        for (int oyt : oy_targets) {
+            TileChoice t{std::max(1, oxt / P0.ax[2].r), std::max(1, oyt / P0.ax[1].r), def.WD};
+            FwdParams P = P0;
+            apply_tiles(P, is3d, t.WX, t.WY, t.WD);
+            if (forward_smem_bytes(P, is3d) > 200 * 1024 || P.OX * P.G > 512) continue;
+            bool dup = false;
+            for (auto& c : cands) dup |= (c.WX == P.WX && c.WY == P.WY);
+            if (!dup) cands.push_back(TileChoice{P.WX, P.WY, t.WD});
+        }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(FCFS_ERR_CUDA, "event create failed");
+    float best = 1e30f;
+    TileChoice pick = def;
+    int tried = 0;
+    for (auto& t : cands) {
+        FwdParams P = P0;
+        apply_tiles(P, is3d, t.WX, t.WY, t.WD);
+        rc = launch_planned(P, ntk, is3d, d->dtype_in, d->dtype_out, st);  // warm-up
+        if (rc) continue;
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps; ++k) launch_planned(P, ntk, is3d, d->dtype_in, d->dtype_out, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        ++tried;
+        if (ms < best) {
+            best = ms;
+            pick = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tuning launches");
+    if (tried == 0) return fail(FCFS_ERR_UNSUPPORTED, "no tile candidate launched");
+    set_plan(P0, d->ndim, d->dtype_in, d->dtype_out, pick);
+    if (best_ms) *best_ms = best;
+    if (n_candidates) *n_candidates = tried;
+    return FCFS_OK;
+}
+
+extern "C" void fcfs_clear_plans(void) { clear_plans(); }

@@ -1,0 +1,247 @@
+"""Python binding of libfcfs: FCFS (arXiv 2203.10670) on GB300.
+
+The C entry points keep their names here (``fcfs_make_weights``,
+``fcfs_geometry``, ``fcfs_forward``, ``fcfs_backward``,
+``fcfs_backward_workspace``, ``fcfs_tune_forward``) and take the same
+arguments.  ``resize`` / ``resize_backward`` / ``FCFSFunction`` / ``FCFS`` are
+thin torch-tensor wrappers around them: they build the descriptor, allocate
+outputs with torch and pass pointers and the current stream.  Every step of
+the layer runs in the CUDA kernels of libfcfs; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import (FCFS_BF16, FCFS_BICUBIC, FCFS_BILINEAR, FCFS_F32, FCFS_NEAREST, FCFS_PAD_CONSTANT,
+                      FCFS_PAD_REFLECT, FCFS_PAD_REPLICATE, FCFS_U8, FCFSError, check)
+
+NEAREST, BILINEAR, BICUBIC = FCFS_NEAREST, FCFS_BILINEAR, FCFS_BICUBIC
+PAD_REPLICATE, PAD_CONSTANT, PAD_REFLECT = FCFS_PAD_REPLICATE, FCFS_PAD_CONSTANT, FCFS_PAD_REFLECT
+
+_DT = {torch.float32: FCFS_F32, torch.bfloat16: FCFS_BF16, torch.uint8: FCFS_U8}
+_TD = {FCFS_F32: torch.float32, FCFS_BF16: torch.bfloat16, FCFS_U8: torch.uint8}
+
+
+@dataclass
+class Axis:
+    """One spatial axis: scale r/s, fixed `method` (w=None) or learnable taps w
+    (float32 CUDA tensor [C, r, 2K+1] per channel or [r, 2K+1] shared)."""
+    r: int
+    s: int
+    method: int = BILINEAR
+    K: int = 0
+    w: Optional[torch.Tensor] = None
+
+
+# ----------------------------------------------------------- raw entry points
+
+def fcfs_make_weights(method: int, r: int, s: int, K: int = 0):
+    """The FP32 weight table W[j][m] (r x (2K+1)) and the K used (K=0 -> K_min)."""
+    lib = N.load()
+    k_out = ctypes.c_int(0)
+    check(lib.fcfs_make_weights(method, r, s, K, None, ctypes.byref(k_out)), "fcfs_make_weights")
+    w = np.zeros((r, 2 * k_out.value + 1), dtype=np.float32)
+    check(lib.fcfs_make_weights(method, r, s, K, w.ctypes.data, ctypes.byref(k_out)), "fcfs_make_weights")
+    return w, k_out.value
+
+
+def fcfs_geometry(method: int, r: int, s: int, K: int, n_in: int):
+    """(n_out, n_windows, left_offset) of one axis."""
+    lib = N.load()
+    no, nw, lo = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+    check(lib.fcfs_geometry(method, r, s, K, n_in, ctypes.byref(no), ctypes.byref(nw), ctypes.byref(lo)),
+          "fcfs_geometry")
+    return no.value, nw.value, lo.value
+
+
+def fcfs_forward(desc: N.fcfs_desc, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    check(N.load().fcfs_forward(ctypes.byref(desc), x_ptr, y_ptr, stream), "fcfs_forward")
+
+
+def fcfs_backward_workspace(desc: N.fcfs_desc) -> int:
+    return int(N.load().fcfs_backward_workspace(ctypes.byref(desc)))
+
+
+def fcfs_backward(desc, x_ptr, gy_ptr, gx_ptr, gw_ptrs, ws_ptr, ws_bytes, stream=0) -> None:
+    arr = None
+    if gw_ptrs is not None:
+        arr = (ctypes.c_void_p * 3)(*(list(gw_ptrs) + [None] * (3 - len(gw_ptrs))))
+    check(N.load().fcfs_backward(ctypes.byref(desc), x_ptr, gy_ptr, gx_ptr,
+                                 ctypes.cast(arr, ctypes.c_void_p) if arr is not None else None,
+                                 ws_ptr, ws_bytes, stream), "fcfs_backward")
+
+
+def fcfs_tune_forward(desc, x_ptr, y_ptr, stream=0, reps=3):
+    """Time the candidate tile shapes and keep the fastest for this key."""
+    ms, n = ctypes.c_float(), ctypes.c_int()
+    check(N.load().fcfs_tune_forward(ctypes.byref(desc), x_ptr, y_ptr, stream, reps, ctypes.byref(ms),
+                                     ctypes.byref(n)), "fcfs_tune_forward")
+    return ms.value, n.value
+
+
+def fcfs_clear_plans() -> None:
+    N.load().fcfs_clear_plans()
+
+
+# ------------------------------------------------------------- descriptors
+
+def out_len(n: int, r: int, s: int) -> int:
+    return (n * r) // s
+
+
+def make_desc(shape: Sequence[int], axes: Sequence[Axis], dtype_in: int, dtype_out: int,
+              pad: int = PAD_REPLICATE, pad_value: float = 0.0) -> N.fcfs_desc:
+    """Descriptor for an input of shape [n, c, *spatial] (spatial outermost first)."""
+    nd = len(shape) - 2
+    if nd != len(axes) or not 1 <= nd <= 3:
+        raise ValueError(f"{len(axes)} axes for a tensor with {nd} spatial dims")
+    d = N.fcfs_desc()
+    d.ndim = nd
+    d.n, d.c = int(shape[0]), int(shape[1])
+    for a, ax in enumerate(axes):
+        d.in_shape[a] = int(shape[2 + a])
+        d.out_shape[a] = out_len(int(shape[2 + a]), ax.r, ax.s)
+        d.axis[a].r, d.axis[a].s = ax.r, ax.s
+        d.axis[a].K, d.axis[a].method = ax.K, ax.method
+        if ax.w is not None:
+            w = ax.w
+            if w.dtype != torch.float32 or not w.is_cuda or not w.is_contiguous():
+                raise ValueError("learnable weights must be contiguous float32 CUDA tensors")
+            if w.shape[-2] != ax.r:
+                raise ValueError("weights must have r rows")
+            T = w.shape[-1]
+            d.axis[a].K = ax.K if ax.K else (T - 1) // 2
+            if 2 * d.axis[a].K + 1 != T:
+                raise ValueError("weights must have 2K+1 taps")
+            d.axis[a].w = w.data_ptr()
+            d.axis[a].w_per_channel = 1 if w.dim() == 3 else 0
+        else:
+            d.axis[a].w = None
+            d.axis[a].w_per_channel = 0
+    d.dtype_in, d.dtype_out = dtype_in, dtype_out
+    d.pad, d.pad_value = pad, float(pad_value)
+    d.align = 0
+    return d
+
+
+def out_shape(shape: Sequence[int], axes: Sequence[Axis]):
+    return tuple(shape[:2]) + tuple(out_len(n, a.r, a.s) for n, a in zip(shape[2:], axes))
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+# ------------------------------------------------------------ tensor level
+
+def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_value: float = 0.0,
+           out_dtype: Optional[torch.dtype] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """y = FCFS(x) for x [n, c, *spatial] (float32, bfloat16 or uint8).
+
+    A CUDA tensor is processed on its device and current stream.  A host tensor
+    is copied to the current CUDA device, resized there, and the result copied
+    back to host memory (pinned inputs make both copies asynchronous)."""
+    if not x.is_cuda:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        y = resize(x.to(dev, non_blocking=True), axes, pad, pad_value, out_dtype)
+        if out is not None:
+            out.copy_(y)
+            return out
+        return y.cpu()
+    if out_dtype is None:
+        out_dtype = torch.float32 if x.dtype == torch.uint8 else x.dtype
+    x = x.contiguous()
+    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value)
+    oshape = out_shape(x.shape, axes)
+    if out is None:
+        out = torch.empty(oshape, dtype=out_dtype, device=x.device)
+    elif tuple(out.shape) != oshape or out.dtype != out_dtype or not out.is_contiguous():
+        raise ValueError("out has the wrong shape, dtype or layout")
+    fcfs_forward(d, x.data_ptr(), out.data_ptr(), _stream(x.device))
+    return out
+
+
+def resize_backward(x: Optional[torch.Tensor], gy: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE,
+                    pad_value: float = 0.0, in_shape=None, in_dtype=None, need_dx: bool = True,
+                    need_dw: Sequence[bool] = ()):
+    """(gx, [gw per axis]) of the FCFS forward for upstream gradient gy."""
+    if in_shape is None:
+        in_shape = tuple(x.shape)
+    if in_dtype is None:
+        in_dtype = x.dtype
+    gy = gy.contiguous()
+    d = make_desc(in_shape, axes, _DT[in_dtype], _DT[gy.dtype], pad, pad_value)
+    dev = gy.device
+    gx = torch.empty(in_shape, dtype=in_dtype, device=dev) if need_dx else None
+    gws, ptrs = [], []
+    for a, ax in enumerate(axes):
+        want = bool(need_dw[a]) if a < len(need_dw) else False
+        if want and ax.w is not None:
+            g = torch.empty_like(ax.w)
+            gws.append(g)
+            ptrs.append(g.data_ptr())
+        else:
+            gws.append(None)
+            ptrs.append(None)
+    ws_bytes = fcfs_backward_workspace(d) if any(p is not None for p in ptrs) else 0
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    fcfs_backward(d, x.data_ptr() if x is not None else None, gy.data_ptr(),
+                  gx.data_ptr() if gx is not None else None, ptrs, ws.data_ptr(), ws_bytes, _stream(dev))
+    return gx, gws
+
+
+class FCFSFunction(torch.autograd.Function):
+    """Differentiable FCFS: hand-written forward and backward kernels of libfcfs."""
+
+    @staticmethod
+    def forward(ctx, x, spec, *weights):
+        axes = [Axis(a.r, a.s, a.method, a.K, w) for a, w in zip(spec["axes"], weights)]
+        y = resize(x, axes, spec["pad"], spec["pad_value"], spec.get("out_dtype"))
+        ctx.spec = spec
+        ctx.save_for_backward(x, *[w if w is not None else torch.empty(0) for w in weights])
+        ctx.has_w = [w is not None for w in weights]
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, *ws = ctx.saved_tensors
+        spec = ctx.spec
+        axes = [Axis(a.r, a.s, a.method, a.K, w if h else None) for a, w, h in zip(spec["axes"], ws, ctx.has_w)]
+        need_w = [h and ctx.needs_input_grad[2 + i] for i, h in enumerate(ctx.has_w)]
+        gx, gws = resize_backward(x if any(need_w) else None, gy.to(spec.get("out_dtype") or x.dtype), axes,
+                                  spec["pad"], spec["pad_value"], in_shape=tuple(x.shape), in_dtype=x.dtype,
+                                  need_dx=ctx.needs_input_grad[0], need_dw=need_w)
+        return (gx, None, *gws)
+
+
+class FCFS(torch.nn.Module):
+    """FCFS layer (Sec. 3.2 / Sec. 4): depthwise, separable per spatial axis.
+
+    ratios: one (r, s) per spatial axis.  learnable=True gives each axis
+    per-channel taps [C, r, 2K+1] initialised to the method's table."""
+
+    def __init__(self, channels: int, ratios, method: int = BILINEAR, pad: int = PAD_REPLICATE,
+                 pad_value: float = 0.0, learnable: bool = False, K: int = 0, out_dtype=None):
+        super().__init__()
+        self.ratios = [tuple(rs) for rs in ratios]
+        self.method, self.pad, self.pad_value, self.out_dtype = method, pad, pad_value, out_dtype
+        self.weights = torch.nn.ParameterList()
+        self.Ks = []
+        for r, s in self.ratios:
+            w, k = fcfs_make_weights(method, r, s, K)
+            self.Ks.append(k)
+            if learnable:
+                self.weights.append(torch.nn.Parameter(torch.from_numpy(np.tile(w[None], (channels, 1, 1)))))
+        self.learnable = learnable
+
+    def forward(self, x):
+        spec = {"axes": [Axis(r, s, self.method, k) for (r, s), k in zip(self.ratios, self.Ks)],
+                "pad": self.pad, "pad_value": self.pad_value, "out_dtype": self.out_dtype}
+        ws = [w.contiguous() for w in self.weights] if self.learnable else [None] * len(self.ratios)
+        return FCFSFunction.apply(x, spec, *ws)

@@ -1,0 +1,159 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+include/fcfs.h declares, computes its host-side tables like the oracle, and
+rejects malformed arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2203_10670_gb300 import build
+
+    build.build()
+    from paper_2203_10670_gb300 import _native
+
+    return _native
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(fcfs_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(native):
+    lib = ctypes.CDLL(native.LIB_PATH)
+    declared = _declared_functions()
+    assert "fcfs_forward" in declared and "fcfs_backward" in declared
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding knows every one of them
+    assert declared <= set(native.SIGNATURES), declared - set(native.SIGNATURES)
+
+
+def test_status_strings(native):
+    lib = native.load()
+    assert lib.fcfs_status_string(0) == b"ok"
+    for code in range(-7, 0):
+        assert lib.fcfs_status_string(code) not in (b"ok", b"unknown status")
+
+
+RATIOS = [(3, 2), (2, 3), (4, 3), (5, 4), (7, 5), (1, 1), (2, 1), (1, 2), (5, 2), (2, 11), (27, 11)]
+
+
+@pytest.mark.parametrize("method", (0, 1, 2))
+@pytest.mark.parametrize("r,s", RATIOS)
+def test_make_weights_matches_oracle_table(orc, native, method, r, s):
+    from paper_2203_10670_gb300 import fcfs
+
+    for extra in (0, 2):
+        K = orc.kmin(method, s) + extra
+        w, k_used = fcfs.fcfs_make_weights(method, r, s, K)
+        want, k2 = orc.make_weights(method, r, s, K)
+        assert k_used == k2 == K
+        # FP64 table rounded once to FP32
+        assert np.array_equal(w, want.astype(np.float32))
+
+
+@pytest.mark.parametrize("method", (0, 1, 2))
+@pytest.mark.parametrize("r,s", RATIOS)
+def test_geometry_matches_oracle(orc, native, method, r, s):
+    from paper_2203_10670_gb300 import fcfs
+
+    for n in (0, 1, 7, 64, 1080, 8192):
+        no, nw, L = fcfs.fcfs_geometry(method, r, s, 0, n)
+        assert no == orc.out_len(n, r, s)
+        assert nw == orc.num_windows(no, r)
+        assert L == orc.left_offset(orc.kmin(method, s), s)
+
+
+def test_make_weights_errors(native):
+    from paper_2203_10670_gb300 import fcfs
+
+    with pytest.raises(native.FCFSError) as e:
+        fcfs.fcfs_make_weights(2, 4, 3, 2)
+    assert e.value.status == native.FCFS_ERR_KERNEL_TOO_SMALL
+    for bad in ((1, 0, 2), (1, 2, 0), (5, 3, 2), (1, 65, 2)):
+        with pytest.raises(native.FCFSError) as e:
+            fcfs.fcfs_make_weights(bad[0], bad[1], bad[2], 0)
+        assert e.value.status == native.FCFS_ERR_ARG
+
+
+def _desc(native, **kw):
+    from paper_2203_10670_gb300 import fcfs
+
+    ax = [fcfs.Axis(3, 2, 1), fcfs.Axis(3, 2, 1)]
+    d = fcfs.make_desc((1, 1, 64, 64), ax, native.FCFS_F32, native.FCFS_F32)
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+BOGUS = 0x1000  # never dereferenced: every case fails validation first
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("ndim", 0, -1), ("ndim", 4, -1), ("n", -1, -1), ("dtype_in", 7, -1), ("dtype_out", 2, -1),
+    ("pad", 3, -1), ("align", 1, -3),
+])
+def test_forward_rejects_bad_descriptor(native, field, value, status):
+    lib = native.load()
+    d = _desc(native, **{field: value})
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == status
+    assert lib.fcfs_last_error() != b""
+
+
+def test_forward_rejects_bad_shapes_and_axes(native):
+    lib = native.load()
+    d = _desc(native)
+    d.out_shape[0] = 97
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_ARG
+    d = _desc(native)
+    d.axis[1].s = 0
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_ARG
+    d = _desc(native)
+    d.axis[0].method, d.axis[0].K = 2, 1
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_KERNEL_TOO_SMALL
+    d = _desc(native)
+    assert lib.fcfs_forward(ctypes.byref(d), None, BOGUS, None) == native.FCFS_ERR_ARG
+    assert lib.fcfs_forward(None, BOGUS, BOGUS, None) == native.FCFS_ERR_ARG
+    d = _desc(native)
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS + 1, BOGUS, None) == native.FCFS_ERR_ARG  # misaligned
+
+
+def test_empty_output_enqueues_nothing(native):
+    # an empty result is valid and returns before any device work
+    lib = native.load()
+    d = _desc(native)
+    d.n = 0
+    assert lib.fcfs_forward(ctypes.byref(d), None, None, None) == native.FCFS_OK
+    from paper_2203_10670_gb300 import fcfs
+
+    d = fcfs.make_desc((2, 3, 1, 1), [fcfs.Axis(1, 2, 1), fcfs.Axis(1, 2, 1)], 0, 0)
+    assert tuple(d.out_shape)[:2] == (0, 0)
+    assert lib.fcfs_forward(ctypes.byref(d), None, None, None) == native.FCFS_OK
+
+
+def test_backward_argument_errors(native):
+    lib = native.load()
+    d = _desc(native)
+    d.dtype_in = native.FCFS_U8
+    assert lib.fcfs_backward(ctypes.byref(d), None, BOGUS, BOGUS, None, None, 0, None) == native.FCFS_ERR_UNSUPPORTED
+    d = _desc(native)
+    gw = (ctypes.c_void_p * 3)(BOGUS, None, None)
+    # gw for an axis without learnable weights
+    assert lib.fcfs_backward(ctypes.byref(d), BOGUS, BOGUS, None, ctypes.cast(gw, ctypes.c_void_p), None, 0,
+                             None) == native.FCFS_ERR_ARG
+    assert lib.fcfs_backward_workspace(ctypes.byref(d)) == 0
