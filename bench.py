@@ -47,6 +47,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-extras", action="store_true", help="skip the BF16 / backward / large-config lines")
+    p.add_argument("--batch", type=int, default=16, help="images per step (16 = the c2 workload; smaller for profiling)")
+    p.add_argument("--only", default=None, help="run one op of the step (bicubic_2_3, bicubic_4_3, nearest_3_2)")
+    p.add_argument("--no-tune", action="store_true", help="skip the tile autotuner (fewer launches under a profiler)")
+    p.add_argument("--dtype", choices=("f32", "bf16"), default="f32")
+    p.add_argument("--backward-only", action="store_true",
+                   help="time only the c3 layer backward (bf16, 5/4 learnable) with --batch images")
     return p.parse_args()
 
 
@@ -193,10 +199,16 @@ def run_ours(args, rank, world, device):
 
     dist = world > 1
     stream = torch.cuda.current_stream(device)
-    shape = inputs.C2["shape"]
-    x = inputs.uniform(shape, inputs.C2["seed"], device=device)
+    global OPS
+    if args.only:
+        OPS = [op for op in OPS if op[0] == args.only]
+    shape = (args.batch,) + tuple(inputs.C2["shape"][1:])
+    tdt = torch.float32 if args.dtype == "f32" else torch.bfloat16
+    esz = 4 if args.dtype == "f32" else 2
+    code = 0 if args.dtype == "f32" else 1
+    x = inputs.uniform(shape, inputs.C2["seed"], device=device, dtype=tdt)
     axes = {name: [fcfs.Axis(r, s, m)] * 2 for name, (r, s), m in OPS}
-    outs = {name: torch.empty(fcfs.out_shape(shape, axes[name]), device=device) for name, _, _ in OPS}
+    outs = {name: torch.empty(fcfs.out_shape(shape, axes[name]), device=device, dtype=tdt) for name, _, _ in OPS}
     pix_step = sum(out_pixels(shape, ratio) for _, ratio, _ in OPS)
 
     def step():
@@ -205,7 +217,9 @@ def run_ours(args, rank, world, device):
 
     # plan the tile shapes once (autotuner), then capture the step in a graph
     for name, _, _ in OPS:
-        d = fcfs.make_desc(shape, axes[name], 0, 0)
+        if args.no_tune:
+            break
+        d = fcfs.make_desc(shape, axes[name], code, code)
         fcfs.fcfs_tune_forward(d, x.data_ptr(), outs[name].data_ptr(), stream.cuda_stream, 3)
     step()
     torch.cuda.synchronize()
@@ -245,7 +259,7 @@ def run_ours(args, rank, world, device):
     for name, ratio, _ in OPS:
         s2 = timed(lambda n=name: fcfs.resize(x, axes[n], out=outs[n]), args.steps, stream)
         per = s2 / args.steps
-        nbytes = x.numel() * 4 + outs[name].numel() * 4
+        nbytes = (x.numel() + outs[name].numel()) * esz
         kern[name] = {"ms": per * 1e3, "bytes": nbytes, "GBps": nbytes / per / 1e9,
                       "Gpix_s": out_pixels(shape, ratio) / per / 1e9}
     dom = max(kern, key=lambda k: kern[k]["ms"])
@@ -276,17 +290,19 @@ def run_ours(args, rank, world, device):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         es = float(t.item())
     e2e = {"value": world * e2e_steps * pix_step / es / 1e9, "unit": "Gpix/s",
-           "h2d_bytes_per_step": x.numel() * 4, "d2h_bytes_per_step": sum(v.numel() * 4 for v in outs.values())}
+           "h2d_bytes_per_step": x.numel() * esz, "d2h_bytes_per_step": sum(v.numel() * esz for v in outs.values())}
 
     line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": 16 * world, "l2": "inputs larger than L2 (398 MB)",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD if (args.batch == 16 and not args.only and args.dtype == "f32")
+                       else f"reduced: batch {args.batch}, ops {[o[0] for o in OPS]}, {args.dtype}",
+                       "global_batch": args.batch * world, "l2": "inputs larger than L2 (398 MB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "kernels": kern, "e2e": e2e, "gpu_launches": args.steps * len(OPS)}
     if clk is not None:
         line["clocks"] = clk
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_extras:
         pix, cs, cores, sample = oracle_sample(1)
         line["cpu_baseline"] = {"value": pix / cs / 1e9, "unit": "Gpix/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
@@ -350,6 +366,27 @@ def extras(fcfs, inputs, device, stream, peak):
     return out
 
 
+def backward_only(args, device):
+    """c3 backward alone (input and weight gradients), for profiling."""
+    from paper_2203_10670_gb300 import build as B
+
+    B.build()
+    from paper_2203_10670_gb300 import fcfs, inputs
+
+    stream = torch.cuda.current_stream(device)
+    s3 = (args.batch,) + tuple(inputs.C3["shape"][1:])
+    W, K = fcfs.fcfs_make_weights(fcfs.BILINEAR, 5, 4)
+    wt = torch.from_numpy(np.tile(W[None], (s3[1], 1, 1))).to(device)
+    ax = [fcfs.Axis(5, 4, fcfs.BILINEAR, K, wt), fcfs.Axis(5, 4, fcfs.BILINEAR, K, wt.clone())]
+    x3 = inputs.normal(s3, inputs.C3["seed"], device=device, dtype=torch.bfloat16)
+    y3 = fcfs.resize(x3, ax)
+    g3 = inputs.normal(tuple(y3.shape), inputs.C3["grad_seed"], device=device, dtype=torch.bfloat16)
+    for _ in range(max(1, args.warmup)):
+        fcfs.resize_backward(x3, g3, ax, need_dx=True, need_dw=[True, True])
+    t = timed(lambda: fcfs.resize_backward(x3, g3, ax, need_dx=True, need_dw=[True, True]), args.steps, stream)
+    print(json.dumps({"mode": "c3 backward", "batch": args.batch, "ms": t / args.steps * 1e3}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -363,6 +400,9 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=device)
     try:
+        if args.backward_only:
+            backward_only(args, device)
+            return
         run_ours(args, rank, world, device)
     finally:
         if world > 1:

@@ -72,6 +72,7 @@ SIGNATURES = {
     "fcfs_tune_forward": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P, _I, ctypes.POINTER(ctypes.c_float),
                                ctypes.POINTER(_I)]),
     "fcfs_clear_plans": (None, []),
+    "fcfs_device_status": (_I, [_I]),
 }
 OPTIONAL = set()
 

@@ -245,7 +245,7 @@ bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t) {
 }
 
 // Derive the tile sizes of P from a choice of windows per tile.
-void apply_tiles(FwdParams& P, bool is3d, int WX, int WY, int WD) {
+void apply_tiles(FwdParams& P, bool is3d, int WX, int WY, int WD, int Gforce) {
     const AxisP &AX = P.ax[2], &AY = P.ax[1], &AD = P.ax[0];
     WX = std::max(1, std::min(WX, AX.n_win));
     WY = std::max(1, std::min(WY, AY.n_win));
@@ -256,7 +256,7 @@ void apply_tiles(FwdParams& P, bool is3d, int WX, int WY, int WD) {
     P.IC = (WX - 1) * AX.s + AX.span;
     P.ICp = P.IC;
     P.IR = (WY - 1) * AY.s + AY.span;
-    int G = std::max(1, (256 + P.OX / 2) / P.OX);
+    int G = Gforce > 0 ? Gforce : std::max(1, (256 + P.OX / 2) / P.OX);
     while (P.OX * G > 512 && G > 1) --G;
     P.G = G;
     P.tiles_x = (AX.n_win + WX - 1) / WX;
@@ -320,6 +320,15 @@ const char* fcfs_status_string(int status) {
 
 const char* fcfs_last_error(void) { return g_last_error.c_str(); }
 
+int fcfs_device_status(int clear) {
+    clear_error();
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
+    const int v = read_status_fwd_tma(clear);
+    if (v < 0) return fail(FCFS_ERR_CUDA, "reading the device status word failed");
+    return v;
+}
+
 int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out) {
     clear_error();
     if (r < 1 || s < 1 || r > kMaxR) return fail(FCFS_ERR_ARG, "r, s must be >= 1 and r <= %d", kMaxR);
@@ -370,7 +379,7 @@ int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
 
     bool all_nearest = true;
     for (int a = 0; a < d->ndim; ++a) all_nearest &= (d->axis[a].w == nullptr && d->axis[a].method == FCFS_NEAREST);
-    if (all_nearest) {
+    if (all_nearest && !(d->ndim <= 2 && tma_eligible(d, x))) {
         NearestParams P;
         memset(&P, 0, sizeof P);
         const int lead = 3 - d->ndim;
@@ -403,11 +412,14 @@ int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
     int ntk;
     rc = build_forward_params(d, x, y, &P, &ntk);
     if (rc) return rc;
-    const bool is3d = d->ndim == 3;
     TileChoice tc;
-    if (!get_plan(P, d->ndim, d->dtype_in, d->dtype_out, &tc)) tc = default_tiles(P, is3d);
-    apply_tiles(P, is3d, tc.WX, tc.WY, tc.WD);
-    return launch_planned(P, ntk, is3d, d->dtype_in, d->dtype_out, st);
+    const bool have = get_plan(P, d->ndim, d->dtype_in, d->dtype_out, &tc);
+    if (!have) {
+        const bool use_tma = d->ndim <= 2 && tma_eligible(d, x);
+        tc = use_tma ? default_tma_tiles(P, dtype_size(d->dtype_in)) : default_tiles(P, d->ndim == 3);
+        tc.tma = use_tma ? 1 : 0;
+    }
+    return launch_choice(d, P, ntk, tc, st);
 }
 
 }  // extern "C"
@@ -659,3 +671,123 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- TMA path
+
+#include <cudaTypedefs.h>
+
+namespace fcfs {
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// The bulk-tensor path needs a 16-byte aligned base, rows whose byte pitch is
+// a multiple of 16, and extents a tensor map can describe.
+bool tma_eligible(const fcfs_desc* d, const void* x) {
+    if (d->ndim > 2) return false;
+    const int es = dtype_size(d->dtype_in);
+    const long long W = d->in_shape[d->ndim - 1];
+    const long long H = d->ndim == 2 ? d->in_shape[0] : 1;
+    if (((uintptr_t)x) % 16) return false;
+    if ((W * es) % 16) return false;
+    if (W >= (1LL << 31) || H >= (1LL << 31) || d->n * d->c >= (1LL << 31)) return false;
+    long long oplane = 1;
+    for (int a = 0; a < d->ndim; ++a) oplane *= d->out_shape[a];
+    if (oplane >= (1LL << 31)) return false;  // 32-bit offsets within an output plane
+    return encode_fn() != nullptr;
+}
+
+static int box_width(int IC, int align) { return (IC + align - 1 + align - 1) / align * align; }
+
+static void tma_sizes(const FwdParams& P, int es, int* BW, int* BH, int* buf_bytes, int* bar_off) {
+    const int align = 16 / es;
+    *BW = box_width(P.IC, align);
+    *BH = P.IR;
+    *buf_bytes = ((*BW) * (*BH) * es + 127) / 128 * 128;
+    size_t off = 2 * (size_t)(*buf_bytes) + (size_t)P.IR * P.OX * 4 + (size_t)(P.ax[2].r + P.ax[1].r) * P.ax[2].nt * 4;
+    *bar_off = (int)((off + 15) / 16 * 16);
+}
+
+// 256-thread CTAs; output columns ~128 (an even count), rows as the
+// shared-memory budget allows (3+ CTAs per SM, tiles of ~16-32 outputs per
+// thread so per-tile work amortizes).
+TileChoice default_tma_tiles(const FwdParams& P0, int es) {
+    FwdParams P = P0;
+    const int rx = P.ax[2].r, ry = P.ax[1].r;
+    int WX = std::max(1, 128 / rx);
+    if ((WX * rx) % 2 && WX > 1) WX -= 1;
+    int WY = std::max(1, 64 / ry);
+    for (int it = 0; it < 64; ++it) {
+        apply_tiles(P, false, WX, WY, 1, 0);
+        int BW, BH, bb, bo;
+        tma_sizes(P, es, &BW, &BH, &bb, &bo);
+        if (BW <= 256 && BH <= 256 && bo + 16 <= 72 * 1024) break;
+        if (BW > 256 && WX > 1) WX = std::max(1, WX * 3 / 4);
+        else if (WY > 1) WY = std::max(1, WY * 3 / 4);
+        else if (WX > 1) WX = std::max(1, WX * 3 / 4);
+        else break;
+    }
+    TileChoice t{WX, WY, 1};
+    t.G = 0;
+    t.tma = 1;
+    return t;
+}
+
+int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T) {
+    memset(T, 0, sizeof(*T));
+    T->P = P;
+    const int es = dtype_size(d->dtype_in);
+    T->align = 16 / es;
+    tma_sizes(P, es, &T->BW, &T->BH, &T->buf_bytes, &T->bar_off);
+    if (T->BW > 256 || T->BH > 256) return fail(FCFS_ERR_UNSUPPORTED, "tile too large for one bulk copy");
+    if (P.OX > 256) return fail(FCFS_ERR_UNSUPPORTED, "tile wider than the CTA");
+    T->ntiles = (long long)P.tiles_x * P.tiles_y * P.planes;
+    if (T->ntiles >= (1LL << 31)) return fail(FCFS_ERR_UNSUPPORTED, "too many tiles");
+    T->threads = 256;
+    const cuuint64_t W = (cuuint64_t)P.ax[2].n_in, H = (cuuint64_t)P.ax[1].n_in;
+    cuuint64_t dims[3] = {W, H, (cuuint64_t)P.planes};
+    cuuint64_t strides[2] = {W * es, W * H * es};
+    cuuint32_t box[3] = {(cuuint32_t)T->BW, (cuuint32_t)T->BH, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = d->dtype_in == FCFS_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : d->dtype_in == FCFS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                              : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    CUresult r = encode_fn()(&T->tmap, dt, 3, const_cast<void*>(P.x), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(FCFS_ERR_UNSUPPORTED, "tensor map encode failed (%d)", (int)r);
+    return FCFS_OK;
+}
+
+// Launch the forward with a tile choice: the TMA-staged persistent kernel
+// when the choice asks for it and the layout allows, else the gather kernel.
+int launch_choice(const fcfs_desc* d, FwdParams& P, int ntk, const TileChoice& t, cudaStream_t st) {
+    const bool is3d = d->ndim == 3;
+    if (t.tma == 1 && !is3d && tma_eligible(d, P.x)) {
+        apply_tiles(P, false, t.WX, t.WY, 1, t.G);
+        TmaFwdParams T;
+        int rc = prepare_tma(d, P, &T);
+        if (rc == FCFS_OK && forward_tma_smem_bytes(T) <= 227 * 1024) {
+            cudaError_t e = launch_forward_tma(T, ntk, d->dtype_in, d->dtype_out, st);
+            return e == cudaSuccess ? FCFS_OK : cuda_fail(e, "forward (bulk-copy) launch");
+        }
+        clear_error();
+    }
+    TileChoice g = t;
+    if (t.tma == 1) g = default_tiles(P, is3d);
+    apply_tiles(P, is3d, g.WX, g.WY, g.WD, t.tma == 1 ? 0 : t.G);
+    return launch_planned(P, ntk, is3d, d->dtype_in, d->dtype_out, st);
+}
+
+}  // namespace fcfs

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include "fcfs.h"
 
 namespace fcfs {
@@ -90,6 +92,19 @@ struct BwdParams {
     long long n;
 };
 
+// TMA-staged persistent forward: FwdParams plus the tensor map of the input
+// viewed as [planes][H][W] and the staging box (BW x BH elements).
+struct TmaFwdParams {
+    CUtensorMap tmap;
+    FwdParams P;
+    int BW, BH;        // box width (multiple of 16 bytes) and height
+    int align;         // elements per 16 bytes of the input type
+    int buf_bytes;     // bytes of one staging buffer (128-byte multiple)
+    int bar_off;       // byte offset of the two mbarriers (16-byte aligned)
+    int threads;       // CTA size
+    long long ntiles;  // tiles_x * tiles_y * planes (< 2^31)
+};
+
 struct NearestParams {
     int r[3], s[3], n_in[3], n_out[3];
     long long planes;
@@ -157,6 +172,9 @@ __host__ __device__ inline WinRange win_range(const AxisP& A, const AdjAxis& J, 
 cudaError_t launch_forward_2d(const FwdParams& P, int nt, int din, int dout, cudaStream_t st);
 cudaError_t launch_forward_3d(const FwdParams& P, int nt, int din, int dout, cudaStream_t st);
 cudaError_t launch_nearest(const NearestParams& P, int din, int dout, cudaStream_t st);
+cudaError_t launch_forward_tma(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st);
+size_t forward_tma_smem_bytes(const TmaFwdParams& T);
+int read_status_fwd_tma(int clear);
 size_t forward_smem_bytes(const FwdParams& P, bool is3d);
 size_t dx_smem_bytes(const BwdParams& P, bool is3d);
 size_t dw_smem_bytes(const BwdParams& P);

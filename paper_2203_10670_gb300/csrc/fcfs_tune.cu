@@ -20,7 +20,7 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     if (!x || !y) return fail(FCFS_ERR_ARG, "x and y must be device pointers");
     bool all_nearest = true;
     for (int a = 0; a < d->ndim; ++a) all_nearest &= (d->axis[a].w == nullptr && d->axis[a].method == FCFS_NEAREST);
-    if (all_nearest) return FCFS_OK;  // the nearest copy kernel has no tile choice
+    if (all_nearest && !tma_eligible(d, x)) return FCFS_OK;  // the nearest gather kernel has no tile choice
     cudaStreamCaptureStatus cs;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
@@ -31,20 +31,39 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     rc = build_forward_params(d, x, y, &P0, &ntk);
     if (rc) return rc;
     const bool is3d = d->ndim == 3;
-    const TileChoice def = default_tiles(P0, is3d);
-    std::vector<TileChoice> cands = {def};
-    const int ox_targets[] = {64, 128, 256};
-    const int oy_targets[] = {8, 16, 32, 64};
+    const bool tma = tma_eligible(d, x);
+    std::vector<TileChoice> cands;
+    TileChoice def = tma ? default_tma_tiles(P0, dtype_size(d->dtype_in)) : default_tiles(P0, is3d);
+    def.tma = tma ? 1 : 0;
+    cands.push_back(def);
+    const int ox_targets[] = {64, 128, 192, 256};
+    const int oy_targets[] = {8, 16, 32, 48, 64};
+    const int ry = P0.ax[1].r;
     for (int oxt : ox_targets)
-        for (int oyt : oy_targets) {
-            TileChoice t{std::max(1, oxt / P0.ax[2].r), std::max(1, oyt / P0.ax[1].r), def.WD};
-            FwdParams P = P0;
-            apply_tiles(P, is3d, t.WX, t.WY, t.WD);
-            if (forward_smem_bytes(P, is3d) > 200 * 1024 || P.OX * P.G > 512) continue;
-            bool dup = false;
-            for (auto& c : cands) dup |= (c.WX == P.WX && c.WY == P.WY);
-            if (!dup) cands.push_back(TileChoice{P.WX, P.WY, t.WD});
-        }
+        for (int oyt : oy_targets)
+            for (int gm = 0; gm < 2; ++gm) {
+                TileChoice t{std::max(1, oxt / P0.ax[2].r), std::max(1, oyt / ry), def.WD};
+                t.tma = def.tma;
+                t.G = gm == 0 ? def.G : (def.G == ry ? 1 : ry);
+                FwdParams P = P0;
+                apply_tiles(P, is3d, t.WX, t.WY, t.WD, t.G);
+                if (P.OX * P.G > 512) continue;
+                if (tma) {
+                    TmaFwdParams T;
+                    if (prepare_tma(d, P, &T) != FCFS_OK || forward_tma_smem_bytes(T) > 200 * 1024) {
+                        clear_error();
+                        continue;
+                    }
+                } else if (forward_smem_bytes(P, is3d) > 200 * 1024) {
+                    continue;
+                }
+                t.WX = P.WX;
+                t.WY = P.WY;
+                t.G = P.G;
+                bool dup = false;
+                for (auto& c : cands) dup |= (c.WX == t.WX && c.WY == t.WY && c.G == t.G && c.tma == t.tma);
+                if (!dup) cands.push_back(t);
+            }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(FCFS_ERR_CUDA, "event create failed");
@@ -53,11 +72,13 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     int tried = 0;
     for (auto& t : cands) {
         FwdParams P = P0;
-        apply_tiles(P, is3d, t.WX, t.WY, t.WD);
-        rc = launch_planned(P, ntk, is3d, d->dtype_in, d->dtype_out, st);  // warm-up
+        rc = launch_choice(d, P, ntk, t, st);  // warm-up
         if (rc) continue;
         cudaEventRecord(e0, st);
-        for (int k = 0; k < reps; ++k) launch_planned(P, ntk, is3d, d->dtype_in, d->dtype_out, st);
+        for (int k = 0; k < reps; ++k) {
+            FwdParams Pk = P0;
+            launch_choice(d, Pk, ntk, t, st);
+        }
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;

@@ -89,6 +89,14 @@ def fcfs_clear_plans() -> None:
     N.load().fcfs_clear_plans()
 
 
+def fcfs_device_status(clear: bool = False) -> int:
+    """Device status word (0 = every bounded wait completed); synchronizes."""
+    v = N.load().fcfs_device_status(1 if clear else 0)
+    if v < 0:
+        check(v, "fcfs_device_status")
+    return v
+
+
 # ------------------------------------------------------------- descriptors
 
 def out_len(n: int, r: int, s: int) -> int:

@@ -86,29 +86,45 @@ RATIOS_2D = [((2, 3), (2, 3)), ((4, 3), (4, 3)), ((3, 2), (3, 2)), ((5, 4), (7, 
              ((27, 11), (2, 11)), ((1, 1), (3, 1)), ((5, 2), (3, 4))]
 
 
+# width 301: rows not a multiple of 16 bytes -> gather-staged kernel;
+# width 304: bulk-copy (TMA) staged persistent kernel
+@pytest.mark.parametrize("width", (301, 304))
 @pytest.mark.parametrize("ry,rx", RATIOS_2D)
 @pytest.mark.parametrize("method", (NEAREST, BILINEAR, BICUBIC))
 @pytest.mark.parametrize("pad", (REPL, CONST, REFL))
-def test_2d_ratios_methods_pads_fp32(F, orc, ry, rx, method, pad):
+def test_2d_ratios_methods_pads_fp32(F, orc, ry, rx, method, pad, width):
     # ragged sizes spanning several tiles in both directions
-    x = inputs.uniform((2, 3, 53, 301), 11 + method)
+    x = inputs.uniform((2, 3, 53, width), 11 + method)
     check_forward(F, orc, x, [F.Axis(*ry, method), F.Axis(*rx, method)], pad, pad_value=0.375)
 
 
+@pytest.mark.parametrize("width", (250, 256))
 @pytest.mark.parametrize("method", (NEAREST, BILINEAR, BICUBIC))
 @pytest.mark.parametrize("ratio", ((2, 3), (4, 3), (3, 2), (5, 4)))
-def test_2d_bf16_storage(F, orc, method, ratio):
-    x = inputs.normal((2, 4, 67, 250), 21, dtype=torch.bfloat16)
-    check_forward(F, orc, x, [F.Axis(*ratio, method)] * 2, REPL)
+@pytest.mark.parametrize("pad", (REPL, REFL))
+def test_2d_bf16_storage(F, orc, method, ratio, width, pad):
+    x = inputs.normal((2, 4, 67, width), 21, dtype=torch.bfloat16)
+    check_forward(F, orc, x, [F.Axis(*ratio, method)] * 2, pad)
+
+
+def test_bf16_constant_pad_is_rounded_to_storage(F, orc):
+    # the constant of the padding is a sample of the padded input, so it takes the input's storage type
+    x = inputs.normal((1, 2, 40, 64), 22, dtype=torch.bfloat16)
+    c = 0.3  # not representable in bf16
+    cb = float(torch.tensor(c).to(torch.bfloat16))
+    y = F.resize(x.cuda(), [F.Axis(4, 3, BICUBIC)] * 2, CONST, c)
+    want = orc.resize(x.double().numpy(), [dict(r=4, s=3, method=BICUBIC)] * 2, pad=CONST, pad_value=cb)
+    assert np.abs(y.double().cpu().numpy() - want).max() <= 1e-2 * float(x.double().abs().max())
 
 
 @pytest.mark.parametrize("din,dout", [(torch.float32, torch.bfloat16), (torch.bfloat16, torch.float32),
                                       (torch.uint8, torch.float32), (torch.uint8, torch.bfloat16)])
-def test_mixed_storage_types(F, orc, din, dout):
+@pytest.mark.parametrize("width", (77, 80))
+def test_mixed_storage_types(F, orc, din, dout, width):
     if din == torch.uint8:
-        x = inputs.uint8_pixels((1, 3, 45, 77), 5)
+        x = inputs.uint8_pixels((1, 3, 45, width), 5)
     else:
-        x = inputs.uniform((1, 3, 45, 77), 5, dtype=din)
+        x = inputs.uniform((1, 3, 45, width), 5, dtype=din)
     for method in (NEAREST, BILINEAR, BICUBIC):
         y = F.resize(x.cuda(), [F.Axis(3, 2, method), F.Axis(2, 3, method)], out_dtype=dout)
         want = orc.resize(x.double().numpy(), [dict(r=3, s=2, method=method), dict(r=2, s=3, method=method)])
@@ -116,10 +132,11 @@ def test_mixed_storage_types(F, orc, din, dout):
         assert err <= TOL[dout]
 
 
+@pytest.mark.parametrize("length", (1031, 1032))
 @pytest.mark.parametrize("ratio", ((3, 2), (2, 3), (5, 4), (7, 5), (27, 11)))
 @pytest.mark.parametrize("method", (NEAREST, BILINEAR, BICUBIC))
-def test_1d(F, orc, ratio, method):
-    x = inputs.uniform((3, 2, 1031), 31)
+def test_1d(F, orc, ratio, method, length):
+    x = inputs.uniform((3, 2, length), 31)
     check_forward(F, orc, x, [F.Axis(*ratio, method)], REFL)
 
 
@@ -141,8 +158,9 @@ def test_learnable_weights(F, orc, per_channel, ratios, K, pad):
     for r, s in ratios:
         shape = (C, r, 2 * K + 1) if per_channel else (r, 2 * K + 1)
         axes.append(F.Axis(r, s, BILINEAR, K, (torch.randn(shape, generator=g) * 0.5).cuda()))
-    x = inputs.normal((2, C, 37, 150), 51)
-    check_forward(F, orc, x, axes, pad, pad_value=0.25)
+    for width in (150, 152):
+        x = inputs.normal((2, C, 37, width), 51)
+        check_forward(F, orc, x, axes, pad, pad_value=0.25)
 
 
 def test_learnable_3d(F, orc):
@@ -154,7 +172,7 @@ def test_learnable_3d(F, orc):
 
 def test_edge_cases(F, orc):
     # tiny inputs (every index is near an edge), single pixels, empty results
-    for shape in ((1, 1, 1, 1), (1, 1, 2, 3), (2, 1, 1, 9), (1, 2, 5, 1)):
+    for shape in ((1, 1, 1, 1), (1, 1, 2, 3), (2, 1, 1, 9), (1, 2, 5, 1), (1, 1, 3, 4), (2, 1, 1, 8), (1, 1, 7, 12)):
         for ratio in ((3, 2), (2, 3), (5, 1), (1, 1)):
             for method in (NEAREST, BILINEAR, BICUBIC):
                 for pad in (REPL, CONST, REFL):
@@ -255,3 +273,8 @@ def test_config5_volume_trilinear_full(F, orc):
     errs = []
     check_forward(F, orc, x, [F.Axis(3, 2, BILINEAR)] * 3, REPL, report=errs)
     print(f"c5 trilinear 3/2 256^3 max|err|/max|x| = {errs[0]:.3e}")
+
+
+def test_device_status_clean(F):
+    # every bounded wait of the bulk-copy kernels completed during this module
+    assert F.fcfs_device_status(clear=True) == 0
