@@ -160,6 +160,33 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
  */
 int fcfs_device_status(int clear);
 
+/*
+ * fcfs_backward without a workspace argument, for callers that must not
+ * allocate device memory: code hosted inside a framework or server that owns
+ * every device allocation through its own pool, fixed-footprint deployments
+ * that reserve all memory up front, and latency-critical loops that cannot
+ * afford the synchronization an allocation call may cause.  The paper has no
+ * counterpart; it is an interface convenience.
+ *
+ * Same arguments and results as fcfs_backward minus (workspace, ws_bytes):
+ * the caller still provides x, gy, gx and the gw buffers.  The weight-gradient
+ * partial sums go to a scratch area compiled into the library: 8 MiB of
+ * device memory that every GPU loading libfcfs keeps until the process exits.
+ * Descriptors whose weight gradient needs more than that (see
+ * fcfs_backward_workspace) fail with FCFS_ERR_NOMEM before anything is
+ * enqueued.  No device memory is allocated or freed by this call.
+ *
+ * The first call on each device performs a one-time set-up (it looks up the
+ * device address of the scratch area); make that first call before any stream
+ * capture.  All calls share the one scratch area, so calls whose work can
+ * overlap on the GPU (different streams, or different host threads, without
+ * ordering between them) race and give wrong weight gradients; serialize them.
+ * Nothing in the area needs clearing between calls: every partial sum is
+ * written before it is read.
+ */
+int fcfs_backward_noalloc(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw,
+                          void* stream);
+
 /* Static text for a status code. */
 const char* fcfs_status_string(int status);
 

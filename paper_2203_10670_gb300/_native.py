@@ -73,6 +73,7 @@ SIGNATURES = {
                                ctypes.POINTER(_I)]),
     "fcfs_clear_plans": (None, []),
     "fcfs_device_status": (_I, [_I]),
+    "fcfs_backward_noalloc": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P, _P, _P]),
 }
 OPTIONAL = set()
 

@@ -77,6 +77,16 @@ def fcfs_backward(desc, x_ptr, gy_ptr, gx_ptr, gw_ptrs, ws_ptr, ws_bytes, stream
                                  ws_ptr, ws_bytes, stream), "fcfs_backward")
 
 
+def fcfs_backward_noalloc(desc, x_ptr, gy_ptr, gx_ptr, gw_ptrs, stream=0) -> None:
+    """fcfs_backward with the library's built-in scratch area instead of a workspace."""
+    arr = None
+    if gw_ptrs is not None:
+        arr = (ctypes.c_void_p * 3)(*(list(gw_ptrs) + [None] * (3 - len(gw_ptrs))))
+    check(N.load().fcfs_backward_noalloc(ctypes.byref(desc), x_ptr, gy_ptr, gx_ptr,
+                                         ctypes.cast(arr, ctypes.c_void_p) if arr is not None else None,
+                                         stream), "fcfs_backward_noalloc")
+
+
 def fcfs_tune_forward(desc, x_ptr, y_ptr, stream=0, reps=3):
     """Time the candidate tile shapes and keep the fastest for this key."""
     ms, n = ctypes.c_float(), ctypes.c_int()
