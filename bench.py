@@ -52,7 +52,8 @@ def parse():
     p.add_argument("--no-tune", action="store_true", help="skip the tile autotuner (fewer launches under a profiler)")
     p.add_argument("--dtype", choices=("f32", "bf16"), default="f32")
     p.add_argument("--backward-only", action="store_true",
-                   help="time only the c3 layer backward (bf16, 5/4 learnable) with --batch images")
+                   help="time only a backward: the c3 layer (bf16, 5/4 learnable) or, with --only, the "
+                        "input gradient of that c2 op (fp32), with --batch images")
     return p.parse_args()
 
 
@@ -327,6 +328,19 @@ def extras(fcfs, inputs, device, stream, peak):
         out[f"bf16_{name}"] = {"ms": t * 1e3, "Gpix_s": out_pixels(shape, (r, s)) / t / 1e9,
                                "hbm_frac": nb / t / 1e9 / peak}
     del xb
+    # backward (input gradient) of the c2 bicubic ops at 1080p, FP32
+    xs = tuple(inputs.C2["shape"])
+    for name, (r, s), m in OPS:
+        if m == fcfs.NEAREST:
+            continue
+        ax = [fcfs.Axis(r, s, m)] * 2
+        gy = inputs.uniform(fcfs.out_shape(xs, ax), 9, device=device)
+        fcfs.resize_backward(None, gy, ax, in_shape=xs, in_dtype=torch.float32)
+        t = timed(lambda: fcfs.resize_backward(None, gy, ax, in_shape=xs, in_dtype=torch.float32), steps, stream) / steps
+        nb = (int(np.prod(xs)) + gy.numel()) * 4
+        out[f"c2_bwd_dx_{name}"] = {"ms": t * 1e3, "Gpix_s": out_pixels(xs, (r, s)) / t / 1e9,
+                                    "hbm_frac": nb / t / 1e9 / peak}
+        del gy
     # c3: 8x64x256^2 bf16, 5/4 learnable per-channel taps
     s3 = inputs.C3["shape"]
     W, K = fcfs.fcfs_make_weights(fcfs.BILINEAR, 5, 4)
@@ -363,7 +377,56 @@ def extras(fcfs, inputs, device, stream, peak):
                     "bwd_dx_ms": tdx * 1e3, "bwd_dx_hbm_frac": nb / tdx / 1e9 / peak}
         del x5, y5
     torch.cuda.empty_cache()
+    out.update(serve_bench(fcfs, inputs, device))
     return out
+
+
+def serve_bench(fcfs, inputs, device, count=None):
+    """c4: continuous-batching server on 10,000 mixed requests (uint8, C=3, H and W
+    log-uniform in [64, 2048], r/s and method uniform), inputs pre-staged on the
+    device.  A closed-loop run (all requests queued at once) gives the saturation
+    rate; open-loop runs replay Poisson arrivals at fractions of it.  Latency is
+    completion host time minus scheduled arrival."""
+    count = count or inputs.C4["count"]
+    reqs = inputs.serving_requests(count, rate_per_s=1.0)  # unit-rate gaps, rescaled per run
+    sizes = [3 * r["H"] * r["W"] for r in reqs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    pool = inputs.uint8_pixels((int(offs[-1]),), inputs.C4["size_seed"], device=device)
+    base = pool.data_ptr()
+    gaps = np.array([r["arrival"] for r in reqs])  # cumulative arrival times at rate 1
+    res = {}
+    for odt, tag in ((torch.float32, "fp32"), (torch.bfloat16, "bf16")):
+        code = 0 if odt == torch.float32 else 1
+        descs = [fcfs.make_desc((1, 3, r["H"], r["W"]), [fcfs.Axis(r["r"], r["s"], r["method"])] * 2, 2, code)
+                 for r in reqs]
+        out_bytes = [3 * (r["H"] * r["r"] // r["s"]) * (r["W"] * r["r"] // r["s"]) * (4 if code == 0 else 2)
+                     for r in reqs]
+
+        def run(rate):
+            with fcfs.Server(max(8 << 30, 64 * max(out_bytes)), max_inflight=64, out_dtype=odt,
+                             tile_budget_per_step=8192, auto_release=True) as sv:
+                t0 = fcfs.Server.clock() + 0.01
+                for k in range(count):
+                    due = t0 if rate is None else t0 + gaps[k] / rate
+                    if rate is not None:
+                        while fcfs.Server.clock() < due:
+                            pass
+                    sv.submit_raw(descs[k], base + int(offs[k]), None, due)
+                sv.drain(120_000)
+                return sv.stats()
+
+        sat = run(None)
+        lam = sat["completed"] / max(sat["wall_s"], 1e-9)
+        res[f"serve_{tag}_saturation"] = {"req_s": lam, "gpix_s": sat["gpix_s"], "p50_ms": sat["p50_ms"],
+                                          "p99_ms": sat["p99_ms"], "steps": sat["steps"]}
+        for frac in (0.5, 0.9):
+            st = run(frac * lam)
+            res[f"serve_{tag}_rate{frac:g}"] = {"req_s": frac * lam, "gpix_s": st["gpix_s"], "p50_ms": st["p50_ms"],
+                                                "p99_ms": st["p99_ms"], "deferred": st["deferred"],
+                                                "max_inflight": st["max_inflight_seen"]}
+    del pool
+    torch.cuda.empty_cache()
+    return res
 
 
 def backward_only(args, device):
@@ -374,6 +437,17 @@ def backward_only(args, device):
     from paper_2203_10670_gb300 import fcfs, inputs
 
     stream = torch.cuda.current_stream(device)
+    if args.only:
+        (name, (r, s), m), = [op for op in OPS if op[0] == args.only]
+        xs = (args.batch,) + tuple(inputs.C2["shape"][1:])
+        ax = [fcfs.Axis(r, s, m)] * 2
+        gy = inputs.uniform(fcfs.out_shape(xs, ax), 9, device=device)
+        for _ in range(max(1, args.warmup)):
+            fcfs.resize_backward(None, gy, ax, in_shape=xs, in_dtype=torch.float32)
+        t = timed(lambda: fcfs.resize_backward(None, gy, ax, in_shape=xs, in_dtype=torch.float32), args.steps, stream)
+        print(json.dumps({"mode": f"c2 input gradient {name}", "batch": args.batch, "ms": t / args.steps * 1e3}),
+              flush=True)
+        return
     s3 = (args.batch,) + tuple(inputs.C3["shape"][1:])
     W, K = fcfs.fcfs_make_weights(fcfs.BILINEAR, 5, 4)
     wt = torch.from_numpy(np.tile(W[None], (s3[1], 1, 1))).to(device)

@@ -187,6 +187,75 @@ int fcfs_device_status(int clear);
 int fcfs_backward_noalloc(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw,
                           void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: a persistent request loop on one stream with continuous batching.
+ * Requests (2D images, fixed methods, mixed sizes and factors) queue on the
+ * host; a worker thread admits them while a parameter slot and pool memory
+ * are free (admission by HBM footprint), and every loop step launches one
+ * grouped kernel over tiles taken round-robin from all admitted requests, so
+ * requests that arrive while others are on the GPU join the next step.  Each
+ * tile is computed exactly as fcfs_forward computes it alone: results do not
+ * depend on the mix.  The library allocates device memory here only, at
+ * create: the output pool (hbm_budget_bytes), parameter slots and two
+ * work-list buffers.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    size_t hbm_budget_bytes;  /* pool for outputs the library places (y == NULL at submit) */
+    int max_inflight;         /* requests admitted at once (1..4096) */
+    int out_dtype;            /* FCFS_F32 or FCFS_BF16 for pooled outputs */
+    int tile_budget_per_step; /* tiles per grouped launch; large requests are chunked */
+    int timeout_ms;           /* default bound of fcfs_serve_drain when it is passed -1 */
+    int auto_release;         /* 1: a pooled output is freed as soon as its request completes */
+} fcfs_serve_config;
+
+typedef struct {
+    long long submitted, completed, deferred, rejected, steps;
+    int max_inflight_seen;
+    double p50_ms, p90_ms, p99_ms, mean_ms; /* completion host time - arrival time */
+    double out_pixels;                      /* output pixels (channels of a pixel counted once) */
+    double bytes_moved;                     /* algorithmic input + output bytes */
+    double wall_s;                          /* first arrival to last completion */
+    double gpix_s, gbytes_s;
+} fcfs_serve_stats_t;
+
+/* Seconds on the steady clock the serving loop stamps latencies with. */
+double fcfs_serve_clock(void);
+
+/* Start a server on `stream` (NULL: the server creates its own).  Allocates
+ * the pool and buffers (FCFS_ERR_NOMEM if the pool does not fit) and starts
+ * the worker thread.  *handle receives the server. */
+int fcfs_serve_create(const fcfs_serve_config* cfg, void* stream, void** handle);
+
+/* Queue one request: d describes a 2D resize with fixed methods; x is DEVICE
+ * input (F32, BF16 or U8), kept valid until the request completes; y is DEVICE
+ * output or NULL to place it in the pool (then d->dtype_out must equal the
+ * server's out_dtype).  arrival_s (fcfs_serve_clock time) is the time latency
+ * is measured from.  *req_id receives the id.  FCFS_ERR_NOMEM when the output
+ * could never fit the pool; FCFS_ERR_ARG / FCFS_ERR_UNSUPPORTED for bad
+ * descriptors. */
+int fcfs_serve_submit(void* h, const fcfs_desc* d, const void* x, void* y, double arrival_s,
+                      unsigned long long* req_id);
+
+/* Non-blocking: up to `max` ids of completed requests (each reported once).
+ * Returns FCFS_OK, or the error that stopped the server. */
+int fcfs_serve_poll(void* h, unsigned long long* done_ids, int max, int* n_done);
+
+/* Device address of a completed request's pooled output (auto_release == 0). */
+int fcfs_serve_result(void* h, unsigned long long id, void** y);
+
+/* Return a completed request's pooled output to the pool (auto_release == 0). */
+int fcfs_serve_release(void* h, unsigned long long id);
+
+/* Wait until every queued request has completed, at most timeout_ms (-1: the
+ * configured timeout); FCFS_ERR_TIMEOUT otherwise.  No GPU wait is unbounded. */
+int fcfs_serve_drain(void* h, int timeout_ms);
+
+/* Counters, latency percentiles and throughput since create. */
+int fcfs_serve_stats(void* h, fcfs_serve_stats_t* out);
+
+/* Stop the worker, wait for the stream, free everything. */
+int fcfs_serve_destroy(void* h);
+
 /* Static text for a status code. */
 const char* fcfs_status_string(int status);
 

@@ -46,15 +46,16 @@ class fcfs_desc(ctypes.Structure):
 class fcfs_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
                 ("out_dtype", ctypes.c_int), ("tile_budget_per_step", ctypes.c_int),
-                ("timeout_ms", ctypes.c_int)]
+                ("timeout_ms", ctypes.c_int), ("auto_release", ctypes.c_int)]
 
 
 class fcfs_serve_stats_t(ctypes.Structure):
-    _fields_ = [("completed", ctypes.c_longlong), ("submitted", ctypes.c_longlong),
-                ("deferred", ctypes.c_longlong), ("steps", ctypes.c_longlong),
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("deferred", ctypes.c_longlong), ("rejected", ctypes.c_longlong), ("steps", ctypes.c_longlong),
                 ("max_inflight_seen", ctypes.c_int), ("p50_ms", ctypes.c_double), ("p90_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("out_pixels", ctypes.c_double),
-                ("bytes_moved", ctypes.c_double), ("busy_s", ctypes.c_double), ("wall_s", ctypes.c_double)]
+                ("bytes_moved", ctypes.c_double), ("wall_s", ctypes.c_double), ("gpix_s", ctypes.c_double),
+                ("gbytes_s", ctypes.c_double)]
 
 
 # every function include/fcfs.h declares: name -> (restype, argtypes)
@@ -74,6 +75,16 @@ SIGNATURES = {
     "fcfs_clear_plans": (None, []),
     "fcfs_device_status": (_I, [_I]),
     "fcfs_backward_noalloc": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P, _P, _P]),
+    "fcfs_serve_clock": (ctypes.c_double, []),
+    "fcfs_serve_create": (_I, [ctypes.POINTER(fcfs_serve_config), _P, ctypes.POINTER(_P)]),
+    "fcfs_serve_submit": (_I, [_P, ctypes.POINTER(fcfs_desc), _P, _P, ctypes.c_double,
+                               ctypes.POINTER(ctypes.c_ulonglong)]),
+    "fcfs_serve_poll": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong), _I, ctypes.POINTER(_I)]),
+    "fcfs_serve_result": (_I, [_P, ctypes.c_ulonglong, ctypes.POINTER(_P)]),
+    "fcfs_serve_release": (_I, [_P, ctypes.c_ulonglong]),
+    "fcfs_serve_drain": (_I, [_P, _I]),
+    "fcfs_serve_stats": (_I, [_P, ctypes.POINTER(fcfs_serve_stats_t)]),
+    "fcfs_serve_destroy": (_I, [_P]),
 }
 OPTIONAL = set()
 

@@ -1,0 +1,636 @@
+// K4 (fast path): persistent, TMA-staged input gradient of the FCFS layer
+// for 1D/2D (the adjoint of the Sec. 3.2 / Sec. 4 map, needed to learn the
+// weights as Sec. 6 proposes).
+//
+// The adjoint of one axis is itself a polyphase operator: its window a has s
+// phases u whose outputs are the extended input indices v = a*s + lo_out + u,
+// and phase u reads g at a*r + lo_in + off[u] + t.  A CTA owns a rectangle of
+// REAL input indices; tiles that touch an edge also evaluate the virtual
+// indices left of 0 / right of N-1 and fold them onto the indices the padding
+// maps them to (replicate: the edge sample, reflect: the mirror, constant:
+// dropped).  Per tile:
+//   stage  g rectangle by a bulk-tensor copy (double-buffered; g outside the
+//          forward output is zero, which is the copy's out-of-range fill),
+//   pass x Fx[gr][v] = sum_t W'x[u][t] g[gr][(a-a0)*r + off[u] + t], fold x,
+//   pass y dx[v][q] = sum_t W'y[u][t] Fx[(a-a0)*r + off[u] + t][q], fold y
+//          (through shared memory on edge tiles), store.
+#include <type_traits>
+
+#include "fcfs_internal.cuh"
+#include "fcfs_tma.cuh"
+
+namespace fcfs {
+
+__device__ int g_status_bwd_tma = 0;
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ float to_f(T v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+__device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_out(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+struct DxGeo {
+    int plane, c, qx0, qy0, nqx, nqy;
+    AxRange X, Y;
+    int gx_al, xoff, gy0;
+};
+
+__device__ __forceinline__ DxGeo dx_geo(const TmaDxParams& T, int tile) {
+    DxGeo g;
+    const int txy = T.qtiles_x * T.qtiles_y;
+    g.plane = tile / txy;
+    const int rem = tile - g.plane * txy;
+    const int ty = rem / T.qtiles_x, tx = rem - ty * T.qtiles_x;
+    g.c = g.plane % T.C;
+    g.qx0 = tx * T.QX;
+    g.qy0 = ty * T.QY;
+    g.nqx = min(T.QX, T.aj[2].n_x - g.qx0);
+    g.nqy = min(T.QY, T.aj[1].n_x - g.qy0);
+    g.X = ax_range(T.aj[2], T.pad, g.qx0, g.qx0 + g.nqx - 1);
+    g.Y = ax_range(T.aj[1], T.pad, g.qy0, g.qy0 + g.nqy - 1);
+    const int gx0 = g.X.alo * T.aj[2].r + T.aj[2].lo_in;
+    g.gx_al = gx0 >= 0 ? (gx0 / T.align) * T.align : -(((-gx0) + T.align - 1) / T.align) * T.align;
+    g.xoff = gx0 - g.gx_al;
+    g.gy0 = g.Y.alo * T.aj[1].r + T.aj[1].lo_in;
+    return g;
+}
+
+template <typename Tg>
+__device__ __forceinline__ void issue(const TmaDxParams& T, const DxGeo& g, void* buf, uint64_t* bar) {
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, (uint32_t)(T.GBW * T.GBH * sizeof(Tg)));
+    tma_load_3d(buf, &T.tmap, g.gx_al, g.gy0, g.plane, bar);
+}
+
+__device__ __forceinline__ float fwd_weight(const AxisP& A, int c, int k) {
+    return A.learn ? A.w[(long long)c * A.w_cstride + k] : A.wf[k];
+}
+
+template <int NT>
+__device__ __forceinline__ void stage_adj_weights(float* dst, const AxisP& A, const AdjP& J, int c) {
+    for (int e = threadIdx.x; e < J.s * NT; e += blockDim.x) {
+        const int u = e / NT, t = e - u * NT;
+        const int k = t < J.ntu[u] ? J.idx[u * kMaxAdjTaps + t] : -1;
+        dst[e] = k >= 0 ? fwd_weight(A, c, k) : 0.f;
+    }
+}
+
+template <int NT, typename Tg, typename Tx>
+__global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__ TmaDxParams T) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const AdjP& JX = T.aj[2];
+    const AdjP& JY = T.aj[1];
+    unsigned char* bufs[2] = {smem_raw, smem_raw + T.buf_bytes};
+    float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
+    float* sWx = reinterpret_cast<float*>(smem_raw + T.w_off);
+    float* sWy = sWx + JX.s * NT;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
+    const int QX = T.QX, GBW = T.GBW, VXcap = T.VXcap;
+    const int G = blockDim.x / QX;
+    const int cl = threadIdx.x % QX, gq = threadIdx.x / QX;
+    const bool active = gq < G;
+    const int Nx = JX.n_x, Ny = JY.n_x;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    // each CTA owns a contiguous run of tiles (same plane for many tiles in a row)
+    const int ntiles = (int)T.ntiles;
+    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+    int tile = blockIdx.x * per;
+    const int tile_end = min(ntiles, tile + per);
+    if (tile >= tile_end) return;
+    if (threadIdx.x == 0) issue<Tg>(T, dx_geo(T, tile), bufs[0], &bars[0]);
+    const bool learn = T.ax[2].learn || T.ax[1].learn;
+    int cur_c = -1;
+    for (int k = 0; tile < tile_end; ++k, ++tile) {
+        const DxGeo geo = dx_geo(T, tile);
+        const Tg* G0 = reinterpret_cast<const Tg*>(bufs[k & 1]);
+        const int next = tile + 1;
+        if (threadIdx.x == 0 && next < tile_end) issue<Tg>(T, dx_geo(T, next), bufs[(k + 1) & 1], &bars[(k + 1) & 1]);
+        if (cur_c < 0 || (learn && geo.c != cur_c)) {
+            stage_adj_weights<NT>(sWx, T.ax[2], JX, geo.c);
+            stage_adj_weights<NT>(sWy, T.ax[1], JY, geo.c);
+            cur_c = geo.c;
+        }
+        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        __syncthreads();
+
+        const int VX = geo.X.vhi - geo.X.vlo + 1;
+        const int nGR = geo.Y.ahi >= geo.Y.alo ? (geo.Y.ahi - geo.Y.alo) * JY.r + JY.span : 0;
+        // ---- pass x: adjoint along x for every staged g row, extended columns [vlo, vhi]
+        if (active) {
+            for (int cx = cl; cx < VX; cx += QX) {
+                const int d = geo.X.vlo + cx - JX.lo_out;
+                const int a = d / JX.s, u = d - a * JX.s;  // d >= 0: vlo >= vmin = lo_out
+                float w[NT];
+#pragma unroll
+                for (int t = 0; t < NT; ++t) w[t] = sWx[u * NT + t];
+                // taps past the phase's own count carry zero weights and stay inside the box
+                const Tg* src = G0 + gq * GBW + geo.xoff + (a - geo.X.alo) * JX.r + JX.off[u];
+                float* dst = sF + gq * VXcap + cx;
+#pragma unroll 2
+                for (int gr = gq; gr < nGR; gr += G) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) acc = fmaf(w[t], to_f<Tg>(src[t]), acc);
+                    *dst = acc;
+                    src += G * GBW;
+                    dst += G * VXcap;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- fold x: virtual columns onto the real column the padding maps them to
+        if (geo.X.left || geo.X.right) {
+            for (int gr = threadIdx.x; gr < nGR; gr += blockDim.x) {
+                float* row = sF + gr * VXcap;
+                // only the virtual columns left of 0 and right of N-1; a target outside this tile's
+                // real columns belongs to (and is folded by) its own tile
+                const int l1 = min(geo.X.vhi, -1), r0 = max(geo.X.vlo, Nx);
+                for (int v = geo.X.vlo; v <= l1; ++v) {
+                    const int q = ext_index(v, Nx, T.pad);
+                    if (q >= geo.qx0 && q < geo.qx0 + geo.nqx) row[q - geo.X.vlo] += row[v - geo.X.vlo];
+                }
+                for (int v = r0; v <= geo.X.vhi; ++v) {
+                    const int q = ext_index(v, Nx, T.pad);
+                    if (q >= geo.qx0 && q < geo.qx0 + geo.nqx) row[q - geo.X.vlo] += row[v - geo.X.vlo];
+                }
+            }
+            __syncthreads();
+        }
+        // ---- pass y: adjoint along y on the real columns of the tile
+        const bool ypath_smem = geo.Y.left || geo.Y.right || !geo.Y.covered;
+        float* sO = reinterpret_cast<float*>(bufs[k & 1]);  // the g tile is consumed
+        const int q = geo.qx0 + cl;
+        const int fcol = q - geo.X.vlo;
+        const bool col_ok = active && cl < geo.nqx;
+        const bool col_has = col_ok && q <= geo.X.vhi;
+        Tx* xcol = static_cast<Tx*>(T.gx) + (long long)geo.plane * Ny * Nx + q;
+        if (col_ok) {
+            for (int u = gq; u < JY.s; u += G) {
+                float w[NT];
+#pragma unroll
+                for (int t = 0; t < NT; ++t) w[t] = sWy[u * NT + t];
+                const float* src = sF + JY.off[u] * VXcap + fcol;
+                for (int a = geo.Y.alo; a <= geo.Y.ahi; ++a, src += JY.r * VXcap) {
+                    const int v = a * JY.s + JY.lo_out + u;
+                    if (v < geo.Y.vlo) continue;
+                    if (v > geo.Y.vhi) break;
+                    float acc = 0.f;
+                    if (col_has) {
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) acc = fmaf(w[t], src[t * VXcap], acc);
+                    }
+                    if (ypath_smem) sO[(v - geo.Y.vlo) * QX + cl] = acc;
+                    else store_out(xcol + (long long)v * Nx, acc);
+                }
+            }
+        }
+        if (ypath_smem) {
+            __syncthreads();
+            if (col_ok) {
+                for (int qy = geo.qy0 + gq; qy < geo.qy0 + geo.nqy; qy += G) {
+                    float acc = (qy >= geo.Y.vlo && qy <= geo.Y.vhi) ? sO[(qy - geo.Y.vlo) * QX + cl] : 0.f;
+                    if (geo.Y.left || geo.Y.right) {
+                        const int l1 = min(geo.Y.vhi, -1), r0 = max(geo.Y.vlo, Ny);
+                        for (int v = geo.Y.vlo; v <= l1; ++v)
+                            if (ext_index(v, Ny, T.pad) == qy) acc += sO[(v - geo.Y.vlo) * QX + cl];
+                        for (int v = r0; v <= geo.Y.vhi; ++v)
+                            if (ext_index(v, Ny, T.pad) == qy) acc += sO[(v - geo.Y.vlo) * QX + cl];
+                    }
+                    store_out(xcol + (long long)qy * Nx, acc);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NT, typename Tg, typename Tx>
+cudaError_t run(const TmaDxParams& T, cudaStream_t st) {
+    const size_t smem = (size_t)T.bar_off + 16;
+    auto k = fcfs_bwd_dx2d_tma<NT, Tg, Tx>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
+    k<<<(unsigned)grid, T.threads, smem, st>>>(T);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int read_status_bwd_tma(int clear) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_status_bwd_tma, sizeof(int)) != cudaSuccess) return -1;
+    if (clear && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_status_bwd_tma, &z, sizeof(int));
+    }
+    return v;
+}
+
+#define FCFS_ADJ_NT_CASES(X) X(2) X(3) X(4) X(6) X(8) X(10) X(12) X(16)
+
+cudaError_t launch_dx_tma(const TmaDxParams& T, int nt, int dg, int dx, cudaStream_t st) {
+    auto go = [&](auto tg, auto tx) -> cudaError_t {
+        using Tg = std::remove_pointer_t<decltype(tg)>;
+        using Tx = std::remove_pointer_t<decltype(tx)>;
+        switch (nt) {
+#define CASE(N) \
+    case N: return run<N, Tg, Tx>(T, st);
+            FCFS_ADJ_NT_CASES(CASE)
+#undef CASE
+            default: return cudaErrorInvalidValue;
+        }
+    };
+    if (dg == FCFS_F32 && dx == FCFS_F32) return go((float*)nullptr, (float*)nullptr);
+    if (dg == FCFS_BF16 && dx == FCFS_BF16) return go((__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fcfs
+
+// ===========================================================================
+// K5 (fast path): weight gradient of learnable taps, 1D/2D.
+//   dWy[jy][t] = sum g[iy*r_y + jy][ox] * U[iy*s_y + off_y[jy] + t][ox],  U = x taps of x~
+//   dWx[jx][t] = sum g[oy][ix*r_x + jx] * V[oy][ix*s_x + off_x[jx] + t],  V = y taps of x~
+// A persistent CTA walks a contiguous run of forward-shaped tiles, stages x~
+// and g by bulk copies, and keeps its dot products in registers across tiles;
+// it writes one record per channel it visits.  A second kernel sums the
+// records of each weight entry in a fixed order (bitwise reproducible).
+// ===========================================================================
+namespace fcfs {
+namespace {
+
+constexpr int kDwMaxPairs = 2;
+
+struct DwGeo {
+    int plane, c, ix0, iy0, nwx, nwy, rows, cols, row0, col0, x_al, xoff, g_al, goff;
+    bool edge;
+};
+
+__device__ __forceinline__ DwGeo dw_geo(const TmaDwParams& T, int tile) {
+    const FwdParams& P = T.P;
+    const AxisP& AY = P.ax[1];
+    const AxisP& AX = P.ax[2];
+    DwGeo g;
+    const int txy = P.tiles_x * P.tiles_y;
+    g.plane = tile / txy;
+    const int rem = tile - g.plane * txy;
+    const int ty = rem / P.tiles_x, tx = rem - ty * P.tiles_x;
+    g.c = g.plane % P.C;
+    g.ix0 = tx * P.WX;
+    g.iy0 = ty * P.WY;
+    g.nwx = min(P.WX, AX.n_win - g.ix0);
+    g.nwy = min(P.WY, AY.n_win - g.iy0);
+    g.cols = (g.nwx - 1) * AX.s + AX.span;
+    g.rows = (g.nwy - 1) * AY.s + AY.span;
+    g.col0 = g.ix0 * AX.s + AX.lo;
+    g.row0 = g.iy0 * AY.s + AY.lo;
+    g.x_al = g.col0 >= 0 ? (g.col0 / T.align) * T.align : -(((-g.col0) + T.align - 1) / T.align) * T.align;
+    g.xoff = g.col0 - g.x_al;
+    const int gc = g.ix0 * AX.r;
+    g.g_al = (gc / T.align) * T.align;
+    g.goff = gc - g.g_al;
+    g.edge = g.col0 < 0 || g.col0 + g.cols > AX.n_in || g.row0 < 0 || g.row0 + g.rows > AY.n_in;
+    return g;
+}
+
+template <typename T>
+__device__ __forceinline__ T from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// padding of an edge x~ tile in shared memory (as the forward)
+template <typename Tin>
+__device__ __forceinline__ void dw_fix_edges(const TmaDwParams& T, const DwGeo& g, Tin* buf, const void* x) {
+    const FwdParams& P = T.P;
+    const int H = P.ax[1].n_in, W = P.ax[2].n_in;
+    const int BW = T.BWx;
+    if (P.pad == FCFS_PAD_REFLECT) {
+        const Tin* xp = static_cast<const Tin*>(x) + (long long)g.plane * H * W;
+        for (int e = threadIdx.x; e < g.rows * BW; e += blockDim.x) {
+            const int ry = e / BW, cx = e - ry * BW;
+            const int sy = ext_index(g.row0 + ry, H, P.pad);
+            const int sx = ext_index(g.x_al + cx, W, P.pad);
+            buf[ry * BW + cx] = xp[(long long)sy * W + sx];
+        }
+        __syncthreads();
+        return;
+    }
+    const bool repl = P.pad == FCFS_PAD_REPLICATE;
+    const Tin cv = from_f<Tin>(P.padv);
+    const int cl = max(0, -g.x_al), cr = max(0, g.x_al + BW - W);
+    if (cl > 0 || cr > 0) {
+        const int ncol = cl + cr;
+        for (int e = threadIdx.x; e < g.rows * ncol; e += blockDim.x) {
+            const int ry = e / ncol, k = e - ry * ncol;
+            const int gy = g.row0 + ry;
+            if (gy < 0 || gy >= H) continue;
+            const int cx = k < cl ? k : BW - cr + (k - cl);
+            const int src = (k < cl ? 0 : W - 1) - g.x_al;
+            buf[ry * BW + cx] = repl ? buf[ry * BW + src] : cv;
+        }
+        __syncthreads();
+    }
+    const int rt = max(0, -g.row0), rb = max(0, g.row0 + g.rows - H);
+    if (rt > 0 || rb > 0) {
+        const int nrow = rt + rb;
+        for (int e = threadIdx.x; e < nrow * BW; e += blockDim.x) {
+            const int k = e / BW, cx = e - k * BW;
+            const int ry = k < rt ? k : g.rows - rb + (k - rt);
+            const int src = (k < rt ? 0 : H - 1) - g.row0;
+            buf[ry * BW + cx] = repl ? buf[src * BW + cx] : cv;
+        }
+        __syncthreads();
+    }
+}
+
+template <int NT, typename Tv>
+__global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__ TmaDwParams T, const void* xptr) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const FwdParams& P = T.P;
+    const AxisP& AY = P.ax[1];
+    const AxisP& AX = P.ax[2];
+    Tv* xb[2] = {reinterpret_cast<Tv*>(smem_raw), reinterpret_cast<Tv*>(smem_raw + T.xbuf_bytes)};
+    Tv* gb[2] = {reinterpret_cast<Tv*>(smem_raw + 2 * T.xbuf_bytes),
+                 reinterpret_cast<Tv*>(smem_raw + 2 * T.xbuf_bytes + T.gbuf_bytes)};
+    float* sH = reinterpret_cast<float*>(smem_raw + T.sh_off);
+    float* sV = reinterpret_cast<float*>(smem_raw + T.sv_off);
+    float* sWx = reinterpret_cast<float*>(smem_raw + T.w_off);
+    float* sWy = sWx + AX.r * NT;
+    float* sRed = reinterpret_cast<float*>(smem_raw + T.red_off);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
+
+    const int OX = P.OX, BWx = T.BWx, BWg = T.BWg, ICp = T.ICp;
+    const int G1 = blockDim.x / OX;
+    const int ox = threadIdx.x % OX, g1 = threadIdx.x / OX;
+    const int jx = ox % AX.r, ixl = ox / AX.r;
+    const bool xact = g1 < G1;
+    const int npair = OX * AY.r;
+    const bool per_channel = AX.w_cstride != 0 || AY.w_cstride != 0;
+    const uint32_t tx_bytes = (uint32_t)(T.BWx * T.BHx + T.BWg * T.BHg) * sizeof(Tv);
+
+    float accx[NT], accy[kDwMaxPairs][NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        accx[t] = 0.f;
+#pragma unroll
+        for (int pp = 0; pp < kDwMaxPairs; ++pp) accy[pp][t] = 0.f;
+    }
+
+    float* recs = T.ws + (long long)blockIdx.x * T.maxseg * T.rec;
+    int* ids = reinterpret_cast<int*>(T.ws + (long long)T.grid * T.maxseg * T.rec) + blockIdx.x * T.maxseg;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int per = (T.ntiles + gridDim.x - 1) / gridDim.x;
+    int tile = blockIdx.x * per;
+    const int tile_end = min(T.ntiles, tile + per);
+    auto issue = [&](int t, int b) {
+        const DwGeo g = dw_geo(T, t);
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bars[b], tx_bytes);
+        tma_load_3d(xb[b], &T.tmap_x, g.x_al, g.row0, g.plane, &bars[b]);
+        tma_load_3d(gb[b], &T.tmap_g, g.g_al, g.iy0 * AY.r, g.plane, &bars[b]);
+    };
+    // write this CTA's accumulated partials as record `seg` for channel c
+    auto flush = [&](int seg, int c) {
+        __syncthreads();
+        if (xact) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) sRed[threadIdx.x * NT + t] = accx[t];
+        }
+        float* ry = sRed + blockDim.x * NT;
+#pragma unroll
+        for (int pp = 0; pp < kDwMaxPairs; ++pp) {
+            const int q = threadIdx.x + pp * blockDim.x;
+            if (q < npair) {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) ry[q * NT + t] = accy[pp][t];
+            }
+        }
+        __syncthreads();
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        const int nx = AX.r * NT, ny = AY.r * NT;
+        const int per_jx = G1 * (OX / AX.r);
+        float* rec = recs + (long long)seg * T.rec;
+        for (int e = warp; e < nx + ny; e += nwarp) {
+            float s = 0.f;
+            if (e < nx) {
+                const int j = e / NT, t = e - j * NT;
+                for (int m = lane; m < per_jx; m += 32) {
+                    const int gg = m / (OX / AX.r), il = m - gg * (OX / AX.r);
+                    s += sRed[(gg * OX + il * AX.r + j) * NT + t];
+                }
+            } else {
+                const int e2 = e - nx, j = e2 / NT, t = e2 - j * NT;
+                for (int o = lane; o < OX; o += 32) s += ry[(j * OX + o) * NT + t];
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+            if (lane == 0) rec[e < nx ? P.ax[1].r * NT + e : e - nx] = s;
+        }
+        if (threadIdx.x == 0) ids[seg] = c;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            accx[t] = 0.f;
+#pragma unroll
+            for (int pp = 0; pp < kDwMaxPairs; ++pp) accy[pp][t] = 0.f;
+        }
+    };
+
+    int seg = 0, cur_c = -1;
+    if (tile < tile_end && threadIdx.x == 0) issue(tile, 0);
+    for (int k = 0; tile < tile_end; ++k, ++tile) {
+        const DwGeo geo = dw_geo(T, tile);
+        Tv* X = xb[k & 1];
+        const Tv* Gt = gb[k & 1];
+        if (threadIdx.x == 0 && tile + 1 < tile_end) issue(tile + 1, (k + 1) & 1);
+        const int ch = per_channel ? geo.c : 0;
+        if (ch != cur_c) {
+            if (cur_c >= 0) flush(seg++, cur_c);
+            for (int e = threadIdx.x; e < AX.r * NT; e += blockDim.x) {
+                const int j = e / NT, t = e - j * NT;
+                sWx[e] = t < AX.nt_src ? (AX.learn ? AX.w[geo.c * AX.w_cstride + j * AX.nt_src + t] : AX.wf[j * AX.nt_src + t]) : 0.f;
+            }
+            for (int e = threadIdx.x; e < AY.r * NT; e += blockDim.x) {
+                const int j = e / NT, t = e - j * NT;
+                sWy[e] = t < AY.nt_src ? (AY.learn ? AY.w[geo.c * AY.w_cstride + j * AY.nt_src + t] : AY.wf[j * AY.nt_src + t]) : 0.f;
+            }
+            cur_c = ch;
+        }
+        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        __syncthreads();
+        if (geo.edge) dw_fix_edges<Tv>(T, geo, X, xptr);
+
+        // U = x taps of every staged row (thread = output column)
+        if (xact && ixl < geo.nwx) {
+            float w[NT];
+#pragma unroll
+            for (int t = 0; t < NT; ++t) w[t] = sWx[jx * NT + t];
+            const Tv* src = X + g1 * BWx + geo.xoff + ixl * AX.s + AX.off[jx];
+            float* dst = sH + g1 * OX + ox;
+            for (int ry = g1; ry < geo.rows; ry += G1) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) acc = fmaf(w[t], to_f<Tv>(src[t]), acc);
+                *dst = acc;
+                src += G1 * BWx;
+                dst += G1 * OX;
+            }
+        }
+        // V = y taps of every staged column (thread = column and phase)
+        const int ncv = geo.cols * AY.r;
+        for (int p = threadIdx.x; p < ncv; p += blockDim.x) {
+            const int jy = p / geo.cols, cx = p - jy * geo.cols;
+            float w[NT];
+#pragma unroll
+            for (int t = 0; t < NT; ++t) w[t] = sWy[jy * NT + t];
+            const Tv* src = X + AY.off[jy] * BWx + geo.xoff + cx;
+            float* dst = sV + jy * ICp + cx;
+            for (int iyl = 0; iyl < geo.nwy; ++iyl) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) acc = fmaf(w[t], to_f<Tv>(src[t * BWx]), acc);
+                *dst = acc;
+                src += AY.s * BWx;
+                dst += AY.r * ICp;
+            }
+        }
+        __syncthreads();
+        // dWx: thread = output column, over its group's rows
+        if (xact && ixl < geo.nwx) {
+            const int nrow = geo.nwy * AY.r;
+            const Tv* gp = Gt + geo.goff + ox;
+            const float* vp = sV + ixl * AX.s + AX.off[jx];
+            for (int oyl = g1; oyl < nrow; oyl += G1) {
+                const float gv = to_f<Tv>(gp[oyl * BWg]);
+                const float* v = vp + oyl * ICp;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) accx[t] = fmaf(gv, v[t], accx[t]);
+            }
+        }
+        // dWy: thread = (column, phase) pairs, over the tile's windows
+#pragma unroll
+        for (int pp = 0; pp < kDwMaxPairs; ++pp) {
+            const int q = threadIdx.x + pp * blockDim.x;
+            if (q < npair) {
+                const int jy = q / OX, o = q - jy * OX;
+                if (o / AX.r < geo.nwx) {
+                    const Tv* gp = Gt + jy * BWg + geo.goff + o;
+                    const float* up = sH + AY.off[jy] * OX + o;
+                    for (int iyl = 0; iyl < geo.nwy; ++iyl) {
+                        const float gv = to_f<Tv>(gp[iyl * AY.r * BWg]);
+                        const float* u = up + iyl * AY.s * OX;
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) accy[pp][t] = fmaf(gv, u[t * OX], accy[pp][t]);
+                    }
+                }
+            }
+        }
+        __syncthreads();  // buffers free for the copies two tiles ahead
+    }
+    if (cur_c >= 0) flush(seg++, cur_c);
+    if (threadIdx.x == 0)
+        for (int s2 = seg; s2 < T.maxseg; ++s2) ids[s2] = -1;
+}
+
+// Fixed-order sum of the records of every weight entry (compensated, then a
+// shuffle tree); one warp per entry.
+__global__ void __launch_bounds__(256) fcfs_dw_reduce_tma(const __grid_constant__ TmaDwParams T) {
+    const FwdParams& P = T.P;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nrec = (long long)T.grid * T.maxseg;
+    const int* ids = reinterpret_cast<const int*>(T.ws + nrec * T.rec);
+    long long base = 0;
+    for (int a = 2; a >= 1; --a) {
+        const AxisP& A = P.ax[a];
+        if (T.gw[a] == nullptr) continue;
+        const long long per = (long long)A.r * A.nt_src;
+        const long long nch = A.w_cstride ? P.C : 1;
+        if (wid >= base + nch * per) {
+            base += nch * per;
+            continue;
+        }
+        const long long idx = wid - base;
+        const int ch = (int)(idx / per);
+        const int jt = (int)(idx - ch * per);
+        const int j = jt / A.nt_src, k = jt - j * A.nt_src;
+        const int roff = (a == 2 ? P.ax[1].r * A.nt : 0) + j * A.nt + k;
+        float s = 0.f, comp = 0.f;
+        for (long long m = lane; m < nrec; m += 32) {
+            const int id = ids[m];
+            if (id < 0 || (A.w_cstride && id != ch)) continue;
+            const float y = T.ws[m * T.rec + roff] - comp;
+            const float tsum = s + y;
+            comp = (tsum - s) - y;
+            s = tsum;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) T.gw[a][idx] = s;
+        return;
+    }
+}
+
+}  // namespace
+
+#define FCFS_DW_NT_CASES(X) X(1) X(2) X(3) X(4) X(5) X(7) X(9)
+
+cudaError_t launch_dw_tma(const TmaDwParams& T, int nt, int dt, cudaStream_t st, const void* x) {
+    const size_t smem = (size_t)T.bar_off + 16;
+    auto go = [&](auto tv) -> cudaError_t {
+        using Tv = std::remove_pointer_t<decltype(tv)>;
+        cudaError_t e = cudaSuccess;
+        switch (nt) {
+#define CASE(N)                                                                                          \
+    case N: {                                                                                            \
+        auto k = fcfs_bwd_dw2d_tma<N, Tv>;                                                               \
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
+        if (e != cudaSuccess) return e;                                                                  \
+        k<<<T.grid, T.threads, smem, st>>>(T, x);                                                        \
+        break;                                                                                           \
+    }
+            FCFS_DW_NT_CASES(CASE)
+#undef CASE
+            default: return cudaErrorInvalidValue;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        long long entries = 0;
+        for (int a = 1; a <= 2; ++a)
+            if (T.gw[a]) entries += (long long)(T.P.ax[a].w_cstride ? T.P.C : 1) * T.P.ax[a].r * T.P.ax[a].nt_src;
+        if (entries == 0) return cudaSuccess;
+        fcfs_dw_reduce_tma<<<(unsigned)((entries * 32 + 255) / 256), 256, 0, st>>>(T);
+        return cudaGetLastError();
+    };
+    if (dt == FCFS_F32) return go((float*)nullptr);
+    if (dt == FCFS_BF16) return go((__nv_bfloat16*)nullptr);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fcfs

@@ -9,124 +9,16 @@
 // y taps from there, and writes each output at its pixel-shuffled position.
 #include <type_traits>
 
-#include "fcfs_internal.cuh"
+#include "fcfs_fwd_tile.cuh"
 
 namespace fcfs {
 
 namespace {
 
-// Per-CTA tap weights for one axis, zero-padded from nt_src to NT taps.
-template <int NT>
-__device__ __forceinline__ void stage_weights(float* dst, const AxisP& A, int c) {
-    const int n = A.r * NT;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int j = k / NT, t = k - j * NT;
-        float v = 0.f;
-        if (t < A.nt_src) {
-            v = A.learn ? A.w[(long long)c * A.w_cstride + j * A.nt_src + t] : A.wf[j * A.nt_src + t];
-        }
-        dst[k] = v;
-    }
-}
-
-// Input tile [rows][cols] of one depth plane, extended coordinates row0/col0,
-// with the padding rule as an index map.  One warp per row, lanes across
-// columns (coalesced).  src_plane == nullptr means the whole plane is the
-// constant pad value (constant padding in depth).
-template <typename Tin>
-__device__ __forceinline__ void load_tile(float* sIn, int pitch, const Tin* src_plane, int H, int W, int row0,
-                                          int col0, int rows, int cols, int pad, float padv) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const bool inside_x = col0 >= 0 && col0 + cols <= W;
-    for (int ry = warp; ry < rows; ry += nwarp) {
-        const int sy = ext_index(row0 + ry, H, pad);
-        float* dst = sIn + ry * pitch;
-        if (src_plane == nullptr || sy < 0) {
-            for (int cx = lane; cx < cols; cx += 32) dst[cx] = padv;
-            continue;
-        }
-        const Tin* src = src_plane + (long long)sy * W;
-        if (inside_x) {
-            const Tin* s0 = src + col0;
-            for (int cx = lane; cx < cols; cx += 32) dst[cx] = load_f(s0 + cx);
-        } else {
-            for (int cx = lane; cx < cols; cx += 32) {
-                const int sx = ext_index(col0 + cx, W, pad);
-                dst[cx] = sx < 0 ? padv : load_f(src + sx);
-            }
-        }
-    }
-}
-
-// x taps: sH[ry][ox] = sum_t wx[jx][t] * sIn[ry][ixl*s + off[jx] + t]
-template <int NT>
-__device__ __forceinline__ void pass_x(float* sH, const float* sIn, const float* sWx, const AxisP& AX,
-                                       int OX, int pitch, int rows, int nwx) {
-    const int ox = threadIdx.x % OX, g = threadIdx.x / OX, G = blockDim.x / OX;
-    const int jx = ox % AX.r, ixl = ox / AX.r;
-    if (ixl >= nwx) return;
-    float w[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) w[t] = sWx[jx * NT + t];
-    const float* base = sIn + ixl * AX.s + AX.off[jx];
-    for (int ry = g; ry < rows; ry += G) {
-        const float* row = base + ry * pitch;
-        float acc = 0.f;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) acc = fmaf(w[t], row[t], acc);
-        sH[ry * OX + ox] = acc;
-    }
-}
-
 template <int NT, typename Tin, typename Tout>
 __global__ void __launch_bounds__(512) fcfs_fwd2d(const __grid_constant__ FwdParams P) {
     extern __shared__ float smem[];
-    const AxisP& AY = P.ax[1];
-    const AxisP& AX = P.ax[2];
-    long long t = blockIdx.x;
-    const int tx = (int)(t % P.tiles_x);
-    t /= P.tiles_x;
-    const int ty = (int)(t % P.tiles_y);
-    const long long plane = t / P.tiles_y;
-    const int c = (int)(plane % P.C);
-
-    float* sWx = smem;
-    float* sWy = sWx + AX.r * NT;
-    float* sIn = sWy + AY.r * NT;
-    float* sH = sIn + P.IR * P.ICp;
-
-    const int ix0 = tx * P.WX, iy0 = ty * P.WY;
-    const int nwx = min(P.WX, AX.n_win - ix0), nwy = min(P.WY, AY.n_win - iy0);
-    const int cols = (nwx - 1) * AX.s + AX.span, rows = (nwy - 1) * AY.s + AY.span;
-    const int col0 = ix0 * AX.s + AX.lo, row0 = iy0 * AY.s + AY.lo;
-
-    stage_weights<NT>(sWx, AX, c);
-    stage_weights<NT>(sWy, AY, c);
-    const Tin* xp = static_cast<const Tin*>(P.x) + plane * (long long)AY.n_in * AX.n_in;
-    load_tile<Tin>(sIn, P.ICp, xp, AY.n_in, AX.n_in, row0, col0, rows, cols, P.pad, P.padv);
-    __syncthreads();
-
-    pass_x<NT>(sH, sIn, sWx, AX, P.OX, P.ICp, rows, nwx);
-    __syncthreads();
-
-    // y taps, written at the pixel-shuffled output position
-    const int OX = P.OX;
-    const int ox = threadIdx.x % OX, g = threadIdx.x / OX, G = blockDim.x / OX;
-    const int gox = ix0 * AX.r + ox;
-    if (ox / AX.r >= nwx || gox >= AX.n_out) return;
-    Tout* yp = static_cast<Tout*>(P.y) + plane * (long long)AY.n_out * AX.n_out + gox;
-    for (int iyl = g; iyl < nwy; iyl += G) {
-        const int oyb = (iy0 + iyl) * AY.r;
-        const int jmax = min(AY.r, AY.n_out - oyb);
-        for (int jy = 0; jy < jmax; ++jy) {
-            const float* col = sH + (iyl * AY.s + AY.off[jy]) * OX + ox;
-            const float* wy = sWy + jy * NT;
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < NT; ++k) acc = fmaf(wy[k], col[k * OX], acc);
-            store_f(yp + (long long)(oyb + jy) * AX.n_out, acc);
-        }
-    }
+    fwd2d_tile<NT, Tin, Tout>(P, blockIdx.x, smem);
 }
 
 // 3D: a CTA owns an (OY x OX) output tile and WD depth windows.  Each input
@@ -185,7 +77,7 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d(const __grid_constant__ FwdPar
             load_tile<Tin>(sIn, P.ICp, sd < 0 ? nullptr : xvol + sd * in_plane, AY.n_in, AX.n_in, row0, col0,
                            rows, cols, P.pad, P.padv);
             __syncthreads();
-            pass_x<NT>(sH, sIn, sWx, AX, OX, P.ICp, rows, nwx);
+            pass_x<NT>(sH, sIn, sWx, AX, OX, P.ICp, rows, nwx, G);
             __syncthreads();
             float* slot = ring + ((next - p_first) % P.ring) * ringsz;
             if (ox / AX.r < nwx) {

@@ -186,20 +186,24 @@ __global__ void __launch_bounds__(256) fcfs_fwd2d_tma(const __grid_constant__ Tm
     }
     __syncthreads();
 
+    // each CTA owns a contiguous run of tiles (same plane for many tiles in a row)
     const int ntiles = (int)T.ntiles;
-    int tile = blockIdx.x;
-    if (tile >= ntiles) return;
+    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+    int tile = blockIdx.x * per;
+    const int tile_end = min(ntiles, tile + per);
+    if (tile >= tile_end) return;
     if (threadIdx.x == 0) issue_tile<Tin>(T, tile_geo(T, tile), buf0, &bars[0]);
+    const bool learn = AX.learn || AY.learn;
     int cur_c = -1;
     float wxr[NT];
-    for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    for (int k = 0; tile < tile_end; ++k, ++tile) {
         const TileGeo geo = tile_geo(T, tile);
         Tin* buf = (k & 1) ? buf1 : buf0;
         // prefetch the next tile into the other buffer (its last reader passed the barrier below)
-        const int next = tile + gridDim.x;
-        if (threadIdx.x == 0 && next < ntiles)
+        const int next = tile + 1;
+        if (threadIdx.x == 0 && next < tile_end)
             issue_tile<Tin>(T, tile_geo(T, next), (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
-        const bool new_c = geo.c != cur_c;
+        const bool new_c = cur_c < 0 || (learn && geo.c != cur_c);
         if (new_c) {  // per-channel (or fixed) taps
             for (int e = threadIdx.x; e < AX.r * NT; e += blockDim.x) {
                 const int j = e / NT, t = e - j * NT;

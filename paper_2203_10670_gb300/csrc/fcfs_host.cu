@@ -324,9 +324,9 @@ int fcfs_device_status(int clear) {
     clear_error();
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
-    const int v = read_status_fwd_tma(clear);
-    if (v < 0) return fail(FCFS_ERR_CUDA, "reading the device status word failed");
-    return v;
+    const int v = read_status_fwd_tma(clear), w = read_status_bwd_tma(clear);
+    if (v < 0 || w < 0) return fail(FCFS_ERR_CUDA, "reading the device status word failed");
+    return v | w;
 }
 
 int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out) {
@@ -461,7 +461,11 @@ int launch_planned(FwdParams& P, int ntk, bool is3d, int din, int dout, cudaStre
 
 // ---------------------------------------------------------------- backward
 
+#include <cudaTypedefs.h>
+
 namespace fcfs {
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 
 // Transposed tap table of one axis (see AdjAxis): entry (k, j, t) of residue u
 // for every tap with relative offset e = off[j] + t = u + k*s.
@@ -571,6 +575,241 @@ void plan_dw(BwdParams& B) {
     B.dw_rec = (P.ax[1].r + P.ax[2].r) * nt;
 }
 
+// Adjoint table of one forward axis in the forward-like form of AdjP.
+// Returns the tap count the kernel must evaluate, or -1 if it does not fit.
+int build_adjp(const AxisP& A, AdjP* J) {
+    memset(J, 0, sizeof(*J));
+    if (A.s > kMaxS) return -1;
+    J->s = A.s;
+    J->r = A.r;
+    J->lo_out = A.lo;
+    J->n_g = A.n_out;
+    J->n_x = A.n_in;
+    int emin[kMaxS], emax[kMaxS], lo_in = INT_MAX, efmax = 0;
+    for (int u = 0; u < A.s; ++u) {
+        emin[u] = INT_MAX;
+        emax[u] = INT_MIN;
+    }
+    for (int j = 0; j < A.r; ++j)
+        for (int t = 0; t < A.nt_src; ++t) {
+            const int e = A.off[j] + t, u = e % A.s, k = e / A.s;
+            const int ep = j - k * A.r;
+            emin[u] = std::min(emin[u], ep);
+            emax[u] = std::max(emax[u], ep);
+            lo_in = std::min(lo_in, ep);
+            efmax = std::max(efmax, e);
+        }
+    int nt = 1;
+    for (int u = 0; u < A.s; ++u)
+        if (emin[u] != INT_MAX) nt = std::max(nt, emax[u] - emin[u] + 1);
+    if (nt > kMaxAdjTaps) return -1;
+    for (int u = 0; u < A.s; ++u) {
+        for (int t = 0; t < kMaxAdjTaps; ++t) J->idx[u * kMaxAdjTaps + t] = -1;
+        if (emin[u] == INT_MAX) {
+            J->off[u] = 0;
+            J->ntu[u] = 0;
+            continue;
+        }
+        J->off[u] = (short)(emin[u] - lo_in);
+        J->ntu[u] = (signed char)(emax[u] - emin[u] + 1);
+    }
+    for (int j = 0; j < A.r; ++j)
+        for (int t = 0; t < A.nt_src; ++t) {
+            const int e = A.off[j] + t, u = e % A.s, k = e / A.s;
+            const int ep = j - k * A.r;
+            J->idx[u * kMaxAdjTaps + (ep - emin[u])] = (short)(j * A.nt_src + t);
+        }
+    J->lo_in = lo_in;
+    J->vmin = A.lo;
+    J->vmax = (A.n_win - 1) * A.s + A.lo + efmax;
+    return nt;
+}
+
+static int adj_template_taps(int nt) {
+    static const int widths[] = {2, 3, 4, 6, 8, 10, 12, 16};
+    for (int w : widths)
+        if (w >= nt) return w;
+    return -1;
+}
+
+// Plan the bulk-copy input-gradient kernel.  Returns FCFS_OK when the path
+// applies (1D/2D, same storage type for g and dx, 16-byte row pitch of g,
+// tables within limits), with *ntk the tap template.
+static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, void* gx, TmaDxParams* T, int* ntk) {
+    if (d->ndim > 2 || d->dtype_in != d->dtype_out || d->dtype_in == FCFS_U8) return -1;
+    const int es = dtype_size(d->dtype_out);
+    const long long Wo = d->out_shape[d->ndim - 1];
+    if (((uintptr_t)gy) % 16 || (Wo * es) % 16) return -1;
+    if (d->n * d->c >= (1LL << 31)) return -1;
+    long long iplane = 1;
+    for (int a = 0; a < d->ndim; ++a) iplane *= d->in_shape[a];
+    if (iplane >= (1LL << 31)) return -1;
+    memset(T, 0, sizeof(*T));
+    int nt = 1;
+    for (int a = 0; a < 3; ++a) {
+        T->ax[a] = B.ax[a];
+        const int n = build_adjp(B.ax[a], &T->aj[a]);
+        if (n < 0) return -1;
+        nt = std::max(nt, n);
+    }
+    const int w = adj_template_taps(nt);
+    if (w < 0) return -1;
+    // padded taps widen the span each adjoint window reads
+    for (int a = 1; a < 3; ++a) {
+        AdjP& J = T->aj[a];
+        J.nt = w;
+        int span = 0;
+        for (int u = 0; u < J.s; ++u) span = std::max(span, J.off[u] + w);
+        J.span = span;
+    }
+    T->C = (int)d->c;
+    T->pad = d->pad;
+    T->align = 16 / es;
+    T->threads = 256;
+    const int Nx = T->aj[2].n_x, Ny = T->aj[1].n_x;
+    T->QX = Nx >= 128 ? 128 : Nx > 64 ? 128 : Nx > 32 ? 64 : 32;
+    T->QY = std::min(32, std::max(1, Ny));
+    for (int it = 0; it < 8; ++it) {
+        // capacities over every tile position of each axis
+        int vx = 1, vy = 1, gw = 1, gh = 1;
+        for (int q0 = 0; q0 < Nx; q0 += T->QX) {
+            const AxRange R = ax_range(T->aj[2], d->pad, q0, std::min(Nx, q0 + T->QX) - 1);
+            vx = std::max(vx, R.vhi - R.vlo + 1);
+            if (R.ahi >= R.alo) gw = std::max(gw, (R.ahi - R.alo) * T->aj[2].r + T->aj[2].span);
+        }
+        for (int q0 = 0; q0 < Ny; q0 += T->QY) {
+            const AxRange R = ax_range(T->aj[1], d->pad, q0, std::min(Ny, q0 + T->QY) - 1);
+            vy = std::max(vy, R.vhi - R.vlo + 1);
+            if (R.ahi >= R.alo) gh = std::max(gh, (R.ahi - R.alo) * T->aj[1].r + T->aj[1].span);
+        }
+        T->VXcap = vx;
+        T->VYcap = vy;
+        T->GBW = (gw + T->align - 1 + T->align - 1) / T->align * T->align;
+        T->GBH = gh;
+        const size_t gbytes = (size_t)T->GBW * T->GBH * es;
+        const size_t obytes = (size_t)T->VYcap * T->QX * 4;
+        T->buf_bytes = (int)((std::max(gbytes, obytes) + 127) / 128 * 128);
+        T->fx_off = 2 * T->buf_bytes;
+        T->w_off = T->fx_off + T->GBH * T->VXcap * 4;
+        T->bar_off = (T->w_off + (T->aj[2].s + T->aj[1].s) * w * 4 + 15) / 16 * 16;
+        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 16 <= 56 * 1024) break;
+        if (T->QX > 64 && T->QX >= 4 * T->QY) T->QX /= 2;
+        else if (T->QY > 8) T->QY /= 2;
+        else if (T->QX > 32) T->QX /= 2;
+        else break;
+    }
+    if (T->GBW > 256 || T->GBH > 256 || T->bar_off + 16 > 200 * 1024) return -1;
+    T->qtiles_x = (Nx + T->QX - 1) / T->QX;
+    T->qtiles_y = (Ny + T->QY - 1) / T->QY;
+    T->ntiles = (long long)T->qtiles_x * T->qtiles_y * d->n * d->c;
+    if (T->ntiles >= (1LL << 31)) return -1;
+    T->gy = gy;
+    T->gx = gx;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return -1;
+    const cuuint64_t Wg = (cuuint64_t)T->aj[2].n_g, Hg = (cuuint64_t)T->aj[1].n_g;
+    cuuint64_t dims[3] = {Wg, Hg, (cuuint64_t)(d->n * d->c)};
+    cuuint64_t strides[2] = {Wg * es, Wg * Hg * es};
+    cuuint32_t box[3] = {(cuuint32_t)T->GBW, (cuuint32_t)T->GBH, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (enc(&T->tmap, dt, 3, const_cast<void*>(gy), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return -1;
+    *ntk = w;
+    return FCFS_OK;
+}
+
+// Plan the bulk-copy weight-gradient kernel (1D/2D, x and gy in the same
+// storage type, 16-byte row pitches).  The grid is fixed by the tile's
+// shared-memory footprint on a 152-SM GB300, so the workspace size and the
+// summation order depend on the descriptor only.
+static int plan_dw_tma(const fcfs_desc* d, const FwdParams& P0, const void* x, const void* gy, TmaDwParams* T,
+                       int* ntk, bool encode) {
+    if (d->ndim > 2 || d->dtype_in != d->dtype_out || d->dtype_in == FCFS_U8) return -1;
+    const int es = dtype_size(d->dtype_in);
+    const long long W = d->in_shape[d->ndim - 1], Wo = d->out_shape[d->ndim - 1];
+    if ((W * es) % 16 || (Wo * es) % 16) return -1;
+    if (encode && (((uintptr_t)x) % 16 || ((uintptr_t)gy) % 16)) return -1;
+    if (d->n * d->c >= (1LL << 31)) return -1;
+    memset(T, 0, sizeof(*T));
+    T->P = P0;
+    FwdParams& P = T->P;
+    const int nt = P.ax[2].nt;
+    const int align = 16 / es;
+    T->align = align;
+    T->threads = 256;
+    int WX = std::max(1, 128 / P.ax[2].r), WY = std::max(1, 32 / P.ax[1].r);
+    for (int it = 0; it < 64; ++it) {
+        apply_tiles(P, false, WX, WY, 1, 0);
+        const int npair = P.OX * P.ax[1].r;
+        T->BWx = (P.IC + align - 1 + align - 1) / align * align;
+        T->BHx = P.IR;
+        T->BWg = (P.OX + align - 1 + align - 1) / align * align;
+        T->BHg = P.OY;
+        T->ICp = P.IC;
+        T->xbuf_bytes = (T->BWx * T->BHx * es + 127) / 128 * 128;
+        T->gbuf_bytes = (T->BWg * T->BHg * es + 127) / 128 * 128;
+        T->sh_off = 2 * T->xbuf_bytes + 2 * T->gbuf_bytes;
+        T->sv_off = T->sh_off + P.IR * P.OX * 4;
+        T->w_off = T->sv_off + P.OY * T->ICp * 4;
+        T->red_off = T->w_off + (P.ax[2].r + P.ax[1].r) * nt * 4;
+        T->bar_off = (T->red_off + (T->threads + npair) * nt * 4 + 15) / 16 * 16;
+        const bool fits = T->BWx <= 256 && T->BHx <= 256 && T->BWg <= 256 && T->BHg <= 256 &&
+                          npair <= 2 * T->threads && P.OX <= T->threads && T->bar_off + 16 <= 64 * 1024;
+        if (fits) break;
+        if (npair > 2 * T->threads && WX > 1) WX = std::max(1, WX * 3 / 4);
+        else if (WY > 1) WY = (WY + 1) / 2;
+        else if (WX > 1) WX = (WX + 1) / 2;
+        else return -1;
+    }
+    const int npair = P.OX * P.ax[1].r;
+    if (npair > 2 * T->threads || P.OX > T->threads || T->bar_off + 16 > 227 * 1024) return -1;
+    const long long ntiles = (long long)P.tiles_x * P.tiles_y * P.planes;
+    if (ntiles >= (1LL << 31)) return -1;
+    T->ntiles = (int)ntiles;
+    const int per_sm = std::max(1, std::min(8, (int)(227 * 1024 / (T->bar_off + 16))));
+    T->grid = (int)std::min<long long>(ntiles, 152LL * per_sm);
+    const int per = (T->ntiles + T->grid - 1) / T->grid;
+    const int tpp = P.tiles_x * P.tiles_y;
+    T->maxseg = (per + tpp - 1) / tpp + 1;
+    T->rec = (P.ax[1].r + P.ax[2].r) * nt;
+    T->n = d->n;
+    *ntk = nt;
+    if (!encode) return FCFS_OK;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return -1;
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint32_t estr[3] = {1, 1, 1};
+    {
+        const cuuint64_t Wx = (cuuint64_t)P.ax[2].n_in, Hx = (cuuint64_t)P.ax[1].n_in;
+        cuuint64_t dims[3] = {Wx, Hx, (cuuint64_t)P.planes};
+        cuuint64_t strides[2] = {Wx * es, Wx * Hx * es};
+        cuuint32_t box[3] = {(cuuint32_t)T->BWx, (cuuint32_t)T->BHx, 1};
+        if (enc(&T->tmap_x, dt, 3, const_cast<void*>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -1;
+    }
+    {
+        const cuuint64_t Wg = (cuuint64_t)P.ax[2].n_out, Hg = (cuuint64_t)P.ax[1].n_out;
+        cuuint64_t dims[3] = {Wg, Hg, (cuuint64_t)P.planes};
+        cuuint64_t strides[2] = {Wg * es, Wg * Hg * es};
+        cuuint32_t box[3] = {(cuuint32_t)T->BWg, (cuuint32_t)T->BHg, 1};
+        if (enc(&T->tmap_g, dt, 3, const_cast<void*>(gy), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -1;
+    }
+    return FCFS_OK;
+}
+
+static size_t dw_tma_workspace(const TmaDwParams& T) {
+    const long long nrec = (long long)T.grid * T.maxseg;
+    return (size_t)((nrec * (T.rec + 1) * sizeof(float) + 255) / 256 * 256);
+}
+
 static size_t dw_workspace(const BwdParams& B) {
     const long long recs = (long long)B.fw.tiles_x * B.fw.tiles_y * B.planes;
     return (size_t)(((recs * B.dw_rec * sizeof(float)) + 255) / 256 * 256);
@@ -593,8 +832,12 @@ size_t fcfs_backward_workspace(const fcfs_desc* d) {
     BwdParams B;
     int ntk;
     if (build_backward_params(d, nullptr, nullptr, nullptr, &B, &ntk) != FCFS_OK) return 0;
+    TmaDwParams T;
+    int ntw = 0;
+    const size_t fast = plan_dw_tma(d, B.fw, nullptr, nullptr, &T, &ntw, false) == FCFS_OK ? dw_tma_workspace(T) : 0;
+    clear_error();
     plan_dw(B);
-    return dw_workspace(B);
+    return std::max(fast, dw_workspace(B));
 }
 
 int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw, void* workspace,
@@ -652,6 +895,16 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
         const long long blocks = (long long)B.fw.tiles_x * B.fw.tiles_y * B.planes;
         if (blocks > INT_MAX || dw_smem_bytes(B) > 227 * 1024) return fail(FCFS_ERR_UNSUPPORTED, "weight-gradient tile too large");
     }
+    if (gx && !is3d) {
+        TmaDxParams T;
+        int ntd = 0;
+        if (plan_dx_tma(d, B, gy, gx, &T, &ntd) == FCFS_OK) {
+            cudaError_t e = launch_dx_tma(T, ntd, d->dtype_out, d->dtype_in, st);
+            if (e != cudaSuccess) return cuda_fail(e, "input-gradient (bulk-copy) launch");
+            gx = nullptr;  // done
+        }
+        clear_error();
+    }
     if (gx) {
         plan_dx(B, is3d);
         if (is3d && B.GDcap > 256) return fail(FCFS_ERR_UNSUPPORTED, "depth ratio needs more than 256 gradient planes per tile");
@@ -662,10 +915,24 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
         if (e != cudaSuccess) return cuda_fail(e, "input-gradient launch");
     }
     if (want_w) {
-        cudaError_t e = launch_dw(B, ntk, d->dtype_in, d->dtype_out, st);
-        if (e != cudaSuccess) return cuda_fail(e, "weight-gradient launch");
-        e = launch_dw_reduce(B, st);
-        if (e != cudaSuccess) return cuda_fail(e, "weight-gradient reduce launch");
+        TmaDwParams T;
+        int ntw = 0;
+        BwdParams B2;
+        int ntk2;
+        build_backward_params(d, x, gy, gx, &B2, &ntk2);
+        if (plan_dw_tma(d, B2.fw, x, gy, &T, &ntw, true) == FCFS_OK && dw_tma_workspace(T) <= ws_bytes) {
+            T.ws = (float*)workspace;
+            const int lead = 3 - d->ndim;
+            for (int a = 0; a < d->ndim; ++a) T.gw[lead + a] = gw[a];
+            cudaError_t e = launch_dw_tma(T, ntw, d->dtype_in, st, x);
+            if (e != cudaSuccess) return cuda_fail(e, "weight-gradient (bulk-copy) launch");
+        } else {
+            clear_error();
+            cudaError_t e = launch_dw(B, ntk, d->dtype_in, d->dtype_out, st);
+            if (e != cudaSuccess) return cuda_fail(e, "weight-gradient launch");
+            e = launch_dw_reduce(B, st);
+            if (e != cudaSuccess) return cuda_fail(e, "weight-gradient reduce launch");
+        }
     }
     return FCFS_OK;
 }
@@ -673,8 +940,6 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
 }  // extern "C"
 
 // ------------------------------------------------------------- TMA path
-
-#include <cudaTypedefs.h>
 
 namespace fcfs {
 

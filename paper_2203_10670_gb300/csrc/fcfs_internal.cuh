@@ -105,6 +105,59 @@ struct TmaFwdParams {
     long long ntiles;  // tiles_x * tiles_y * planes (< 2^31)
 };
 
+// Adjoint of one axis as a forward-like polyphase operator: window a of the
+// adjoint has s phases u, its outputs are the extended input indices
+// v = a*s + lo_out + u, and phase u reads the g positions
+// a*r + lo_in + off[u] + t, t < ntu[u] (tap t of phase u is the forward
+// weight number idx[u][t] = j*nt_src + t_fwd, or -1 for a zero).
+constexpr int kMaxAdjTaps = 16;
+struct AdjP {
+    int s, r;          // adjoint phases per window / g stride per window
+    int lo_in, lo_out;
+    int span;          // g positions one adjoint window reads (taps padded to nt)
+    int nt;            // template tap count
+    int n_g, n_x;      // g length (forward output) and real x length (forward input)
+    int vmin, vmax;    // extended indices the forward touches
+    short off[kMaxS];
+    signed char ntu[kMaxS];
+    short idx[kMaxS * kMaxAdjTaps];
+};
+
+// Bulk-copy staged input-gradient parameters (1D/2D).
+struct TmaDxParams {
+    CUtensorMap tmap;   // gy viewed as [planes][Ho][Wo]
+    AxisP ax[3];        // forward axes (weights)
+    AdjP aj[3];         // adjoint tables
+    int C, pad;
+    int QX, QY;         // real input indices per tile
+    int qtiles_x, qtiles_y;
+    int GBW, GBH;       // g box (width a multiple of 16 bytes)
+    int align;          // g elements per 16 bytes
+    int VXcap, VYcap;   // virtual columns / rows a tile may evaluate
+    int buf_bytes, fx_off, w_off, bar_off;
+    int threads;
+    long long ntiles;
+    const void* gy;
+    void* gx;
+};
+
+// Bulk-copy staged weight-gradient parameters (1D/2D): forward tile
+// geometry, tensor maps of x and gy, and the record layout of the partials.
+struct TmaDwParams {
+    CUtensorMap tmap_x;   // x  as [planes][H][W]
+    CUtensorMap tmap_g;   // gy as [planes][Ho][Wo]
+    FwdParams P;
+    int BWx, BHx, BWg, BHg;  // boxes (widths multiples of 16 bytes)
+    int align;               // elements per 16 bytes (x and gy share the storage type)
+    int xbuf_bytes, gbuf_bytes, sh_off, sv_off, w_off, red_off, bar_off;
+    int ICp;                 // pitch of the V intermediate
+    int threads, maxseg, rec;  // CTA size, records per CTA, floats per record
+    int ntiles, grid;
+    float* ws;               // [grid][maxseg][rec] floats, then [grid][maxseg] plane ids
+    float* gw[3];
+    long long n;
+};
+
 struct NearestParams {
     int r[3], s[3], n_in[3], n_out[3];
     long long planes;
@@ -168,6 +221,36 @@ __host__ __device__ inline WinRange win_range(const AxisP& A, const AdjAxis& J, 
     return w;
 }
 
+__host__ __device__ inline int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Extended-index range [vlo, vhi] a tile of real indices [q0, q1] evaluates,
+// the adjoint windows [alo, ahi] that produce it, and whether the tile takes
+// the virtual indices beyond either edge.
+struct AxRange {
+    int vlo, vhi, alo, ahi;
+    bool left, right, covered;
+};
+
+__host__ __device__ inline AxRange ax_range(const AdjP& J, int pad, int q0, int q1) {
+    AxRange R;
+    const int N = J.n_x;
+    R.left = pad != FCFS_PAD_CONSTANT && J.vmin < 0 && q0 <= -J.vmin;
+    const int rlim = imin(N - 1, 2 * (N - 1) - J.vmax);
+    R.right = pad != FCFS_PAD_CONSTANT && J.vmax > N - 1 && q1 >= rlim;
+    R.vlo = imax(R.left ? J.vmin : q0, J.vmin);
+    R.vhi = imin(R.right ? J.vmax : q1, J.vmax);
+    R.covered = q1 <= R.vhi;
+    if (R.vlo > R.vhi) {
+        R.alo = 0;
+        R.ahi = -1;
+        R.vhi = R.vlo - 1;
+    } else {
+        R.alo = floordiv(R.vlo - J.lo_out, J.s);
+        R.ahi = floordiv(R.vhi - J.lo_out, J.s);
+    }
+    return R;
+}
+
 // host-side launchers (fcfs_fwd.cu / fcfs_bwd.cu)
 cudaError_t launch_forward_2d(const FwdParams& P, int nt, int din, int dout, cudaStream_t st);
 cudaError_t launch_forward_3d(const FwdParams& P, int nt, int din, int dout, cudaStream_t st);
@@ -175,6 +258,9 @@ cudaError_t launch_nearest(const NearestParams& P, int din, int dout, cudaStream
 cudaError_t launch_forward_tma(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st);
 size_t forward_tma_smem_bytes(const TmaFwdParams& T);
 int read_status_fwd_tma(int clear);
+int read_status_bwd_tma(int clear);
+cudaError_t launch_dx_tma(const TmaDxParams& T, int nt, int dg, int dx, cudaStream_t st);
+cudaError_t launch_dw_tma(const TmaDwParams& T, int nt, int dt, cudaStream_t st, const void* x);
 size_t forward_smem_bytes(const FwdParams& P, bool is3d);
 size_t dx_smem_bytes(const BwdParams& P, bool is3d);
 size_t dw_smem_bytes(const BwdParams& P);

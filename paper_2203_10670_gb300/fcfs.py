@@ -263,3 +263,105 @@ class FCFS(torch.nn.Module):
                 "pad": self.pad, "pad_value": self.pad_value, "out_dtype": self.out_dtype}
         ws = [w.contiguous() for w in self.weights] if self.learnable else [None] * len(self.ratios)
         return FCFSFunction.apply(x, spec, *ws)
+
+
+# ----------------------------------------------------------------- serving
+
+class _DeviceArray:
+    """Minimal __cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr: int, shape, dtype: torch.dtype):
+        typestr = {torch.float32: "<f4", torch.bfloat16: "<i2", torch.uint8: "|u1"}[dtype]
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": tuple(shape), "typestr": typestr,
+                                         "version": 3, "strides": None}
+
+
+class Server:
+    """Continuous-batching FCFS server (fcfs_serve_* of libfcfs).
+
+    Requests are 2D images x [1, C, H, W] (uint8, float32 or bfloat16 CUDA
+    tensors, kept alive by the server until they complete) resized by one
+    (r, s) factor and fixed method on both axes."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 64, out_dtype=torch.float32,
+                 tile_budget_per_step: int = 4096, timeout_ms: int = 60_000, auto_release: bool = True,
+                 stream: Optional[torch.cuda.Stream] = None):
+        self._lib = N.load()
+        cfg = N.fcfs_serve_config()
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.max_inflight = int(max_inflight)
+        cfg.out_dtype = _DT[out_dtype]
+        cfg.tile_budget_per_step = int(tile_budget_per_step)
+        cfg.timeout_ms = int(timeout_ms)
+        cfg.auto_release = 1 if auto_release else 0
+        self.out_dtype = out_dtype
+        self._h = ctypes.c_void_p()
+        check(self._lib.fcfs_serve_create(ctypes.byref(cfg), stream.cuda_stream if stream is not None else None,
+                                          ctypes.byref(self._h)), "fcfs_serve_create")
+        self._keep = {}
+        self._shapes = {}
+
+    @staticmethod
+    def clock() -> float:
+        return N.load().fcfs_serve_clock()
+
+    def submit(self, x: torch.Tensor, ratio, method: int = BILINEAR, y: Optional[torch.Tensor] = None,
+               arrival: Optional[float] = None, pad: int = PAD_REPLICATE, pad_value: float = 0.0) -> int:
+        r, s = ratio
+        axes = [Axis(r, s, method)] * 2
+        dout = _DT[y.dtype] if y is not None else _DT[self.out_dtype]
+        d = make_desc(x.shape, axes, _DT[x.dtype], dout, pad, pad_value)
+        rid = ctypes.c_ulonglong()
+        t = self.clock() if arrival is None else float(arrival)
+        check(self._lib.fcfs_serve_submit(self._h, ctypes.byref(d), x.data_ptr(),
+                                          y.data_ptr() if y is not None else None, t, ctypes.byref(rid)),
+              "fcfs_serve_submit")
+        self._keep[rid.value] = (x, y)
+        self._shapes[rid.value] = out_shape(x.shape, axes)
+        return rid.value
+
+    def submit_raw(self, desc: N.fcfs_desc, x_ptr: int, y_ptr: Optional[int], arrival: float) -> int:
+        """fcfs_serve_submit with a prebuilt descriptor (the caller keeps x alive)."""
+        rid = ctypes.c_ulonglong()
+        check(self._lib.fcfs_serve_submit(self._h, ctypes.byref(desc), x_ptr, y_ptr, float(arrival),
+                                          ctypes.byref(rid)), "fcfs_serve_submit")
+        return rid.value
+
+    def poll(self, max_ids: int = 4096):
+        ids = (ctypes.c_ulonglong * max_ids)()
+        n = ctypes.c_int()
+        check(self._lib.fcfs_serve_poll(self._h, ids, max_ids, ctypes.byref(n)), "fcfs_serve_poll")
+        out = [ids[k] for k in range(n.value)]
+        for rid in out:
+            self._keep.pop(rid, None)
+        return out
+
+    def result(self, rid: int) -> torch.Tensor:
+        """Zero-copy view of a pooled output (servers created with auto_release=False)."""
+        p = ctypes.c_void_p()
+        check(self._lib.fcfs_serve_result(self._h, rid, ctypes.byref(p)), "fcfs_serve_result")
+        view = torch.as_tensor(_DeviceArray(p.value, self._shapes[rid], self.out_dtype), device="cuda")
+        return view.view(torch.bfloat16) if self.out_dtype == torch.bfloat16 else view
+
+    def release(self, rid: int) -> None:
+        check(self._lib.fcfs_serve_release(self._h, rid), "fcfs_serve_release")
+
+    def drain(self, timeout_ms: int = -1) -> None:
+        check(self._lib.fcfs_serve_drain(self._h, timeout_ms), "fcfs_serve_drain")
+
+    def stats(self) -> dict:
+        st = N.fcfs_serve_stats_t()
+        check(self._lib.fcfs_serve_stats(self._h, ctypes.byref(st)), "fcfs_serve_stats")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            check(self._lib.fcfs_serve_destroy(self._h), "fcfs_serve_destroy")
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
