@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--only", default=None, help="run one op of the step (bicubic_2_3, bicubic_4_3, nearest_3_2)")
     p.add_argument("--no-tune", action="store_true", help="skip the tile autotuner (fewer launches under a profiler)")
     p.add_argument("--dtype", choices=("f32", "bf16"), default="f32")
+    p.add_argument("--no-graph", action="store_true",
+                   help="launch the step eagerly instead of replaying its CUDA graph (for kernel launch lists)")
     p.add_argument("--backward-only", action="store_true",
                    help="time only a backward: the c3 layer (bf16, 5/4 learnable) or, with --only, the "
                         "input gradient of that c2 op (fp32), with --batch images")
@@ -224,15 +226,18 @@ def run_ours(args, rank, world, device):
         fcfs.fcfs_tune_forward(d, x.data_ptr(), outs[name].data_ptr(), stream.cuda_stream, 3)
     step()
     torch.cuda.synchronize()
-    side = torch.cuda.Stream(device)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(side):
-        with torch.cuda.graph(graph, stream=side):
-            step()
-    torch.cuda.synchronize()
+    if args.no_graph:
+        replay = step
+    else:
+        side = torch.cuda.Stream(device)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                step()
+        torch.cuda.synchronize()
 
-    def replay():
-        graph.replay()
+        def replay():
+            graph.replay()
 
     for _ in range(max(3, args.warmup)):
         replay()
@@ -296,7 +301,8 @@ def run_ours(args, rank, world, device):
     line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD if (args.batch == 16 and not args.only and args.dtype == "f32")
+            "config": {"workload": WORKLOAD if (args.batch == 16 and not args.only and args.dtype == "f32"
+                                                and not args.no_graph)
                        else f"reduced: batch {args.batch}, ops {[o[0] for o in OPS]}, {args.dtype}",
                        "global_batch": args.batch * world, "l2": "inputs larger than L2 (398 MB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
