@@ -1,348 +1,49 @@
-// K1 (fast path): persistent, TMA-staged, double-buffered fused FCFS forward
-// for 1D/2D (Sec. 3.2 pseudocode; Sec. 4 with separable kernels).
-//
-// Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...  While it
-// computes tile k from one shared-memory buffer, the bulk-tensor copy of
-// tile k+1 lands in the other.  Per tile:
-//   stage   x~ tile (TMA box of the [planes][H][W] input; padding applied in
-//           shared memory on edge tiles: replicate/constant fix-up, reflect
-//           by a gather),
-//   pass x  sH[ry][ox] = sum_t Wx[jx][t] x~[ry][ixl*s_x + off_x[jx] + t]
-//           (thread = output column; its taps sit in registers),
-//   pass y  y[oy][ox]  = sum_t Wy[jy][t] sH[iyl*s_y + off_y[jy] + t][ox]
-//           (thread = output column and phase jy; taps in registers), stored
-//           at the pixel-shuffled position: the r-channel hidden layer is
-//           never written.
-// Accumulators start at -0.0 so a single tap of weight 1 (nearest) is an
-// exact copy, signed zeros included.
-#include <type_traits>
-
+// Dispatch of the bulk-copy forward over its per-input-type translation units.
 #include "fcfs_internal.cuh"
-#include "fcfs_tma.cuh"
 
 namespace fcfs {
 
-// Device status word of this translation unit's kernels (bounded waits).
-__device__ int g_status_fwd_tma = 0;
+cudaError_t launch_forward_tma_f32(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st);
+cudaError_t launch_forward_tma_bf16(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st);
+cudaError_t launch_forward_tma_u8(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st);
+cudaError_t launch_forward_rs_f32(const TmaFwdParams& T, int R, int span, cudaStream_t st);
+cudaError_t launch_forward_rs_bf16(const TmaFwdParams& T, int R, int span, cudaStream_t st);
+int read_status_fwd_tma_f32(int clear);
+int read_status_fwd_tma_bf16(int clear);
+int read_status_fwd_tma_u8(int clear);
 
-namespace {
-
-template <typename T>
-__device__ __forceinline__ float to_f(T v);
-template <>
-__device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <>
-__device__ __forceinline__ float to_f<uint8_t>(uint8_t v) { return (float)v; }
-
-template <typename T>
-__device__ __forceinline__ T from_f(float v);
-template <>
-__device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-template <>
-__device__ __forceinline__ uint8_t from_f<uint8_t>(float v) {
-    return (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
-}
-
-template <typename T>
-__device__ __forceinline__ T ldg_raw(const T* p) { return *p; }
-
-struct TileGeo {
-    int plane, c, ix0, iy0, nwx, nwy, rows, cols, row0, col0, x_al, xoff;
-    bool edge;
-};
-
-// Tile index -> geometry, 32-bit arithmetic (the planner keeps the tile count
-// below 2^31).
-__device__ __forceinline__ TileGeo tile_geo(const TmaFwdParams& T, int tile) {
-    const FwdParams& P = T.P;
-    const AxisP& AY = P.ax[1];
-    const AxisP& AX = P.ax[2];
-    TileGeo g;
-    const int txy = P.tiles_x * P.tiles_y;
-    g.plane = tile / txy;
-    const int rem = tile - g.plane * txy;
-    const int ty = rem / P.tiles_x;
-    const int tx = rem - ty * P.tiles_x;
-    g.c = g.plane % P.C;
-    g.ix0 = tx * P.WX;
-    g.iy0 = ty * P.WY;
-    g.nwx = min(P.WX, AX.n_win - g.ix0);
-    g.nwy = min(P.WY, AY.n_win - g.iy0);
-    g.cols = (g.nwx - 1) * AX.s + AX.span;
-    g.rows = (g.nwy - 1) * AY.s + AY.span;
-    g.col0 = g.ix0 * AX.s + AX.lo;
-    g.row0 = g.iy0 * AY.s + AY.lo;
-    // innermost TMA coordinate rounded down to a 16-byte boundary
-    g.x_al = g.col0 >= 0 ? (g.col0 / T.align) * T.align : -(((-g.col0) + T.align - 1) / T.align) * T.align;
-    g.xoff = g.col0 - g.x_al;
-    g.edge = g.col0 < 0 || g.col0 + g.cols > AX.n_in || g.row0 < 0 || g.row0 + g.rows > AY.n_in;
-    return g;
-}
-
-template <typename Tin>
-__device__ __forceinline__ void issue_tile(const TmaFwdParams& T, const TileGeo& g, Tin* buf, uint64_t* bar) {
-    fence_proxy_async_smem();
-    mbar_expect_tx(bar, (uint32_t)(T.BW * T.BH * sizeof(Tin)));
-    tma_load_3d(buf, &T.tmap, g.x_al, g.row0, g.plane, bar);
-}
-
-// Padding on an edge tile, in shared memory.  Replicate and constant use the
-// in-tile samples the TMA box already holds; reflect (whose mirror may leave
-// the box) re-gathers the tile from global memory through the index map.
-template <typename Tin>
-__device__ __forceinline__ void fix_edges(const TmaFwdParams& T, const TileGeo& g, Tin* buf) {
-    const FwdParams& P = T.P;
-    const int H = P.ax[1].n_in, W = P.ax[2].n_in;
-    const int BW = T.BW;
-    if (P.pad == FCFS_PAD_REFLECT) {
-        const Tin* xp = static_cast<const Tin*>(P.x) + g.plane * (long long)H * W;
-        for (int e = threadIdx.x; e < g.rows * BW; e += blockDim.x) {
-            const int ry = e / BW, cx = e - ry * BW;
-            const int sy = ext_index(g.row0 + ry, H, P.pad);
-            const int sx = ext_index(g.x_al + cx, W, P.pad);
-            buf[ry * BW + cx] = ldg_raw(xp + (long long)sy * W + sx);
-        }
-        __syncthreads();
-        return;
-    }
-    const bool repl = P.pad == FCFS_PAD_REPLICATE;
-    const Tin cv = from_f<Tin>(P.padv);
-    // columns outside [0, W) on in-range rows
-    const int cl = max(0, -g.x_al);                 // box columns left of 0
-    const int cr = max(0, g.x_al + BW - W);         // box columns right of W-1
-    if (cl > 0 || cr > 0) {
-        const int ncol = cl + cr;
-        for (int e = threadIdx.x; e < g.rows * ncol; e += blockDim.x) {
-            const int ry = e / ncol, k = e - ry * ncol;
-            const int gy = g.row0 + ry;
-            if (gy < 0 || gy >= H) continue;
-            const int cx = k < cl ? k : BW - cr + (k - cl);
-            const int src = (k < cl ? 0 : W - 1) - g.x_al;
-            buf[ry * BW + cx] = repl ? buf[ry * BW + src] : cv;
-        }
-        __syncthreads();
-    }
-    // rows outside [0, H): copies of the edge rows, or the constant
-    const int rt = max(0, -g.row0), rb = max(0, g.row0 + g.rows - H);
-    if (rt > 0 || rb > 0) {
-        const int nrow = rt + rb;
-        for (int e = threadIdx.x; e < nrow * BW; e += blockDim.x) {
-            const int k = e / BW, cx = e - k * BW;
-            const int ry = k < rt ? k : g.rows - rb + (k - rt);
-            const int src = (k < rt ? 0 : H - 1) - g.row0;
-            buf[ry * BW + cx] = repl ? buf[src * BW + cx] : cv;
-        }
-        __syncthreads();
-    }
-}
-
-// Store of two adjacent outputs (8-byte aligned for float, 4-byte for bf16).
-__device__ __forceinline__ void store2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
-__device__ __forceinline__ void store2(__nv_bfloat16* p, float a, float b) {
-    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
-}
-
-// VEC2: the y pass handles two adjacent output columns per thread (8-byte
-// shared loads, paired global stores); needs an even tile width and an even
-// output row length.
-template <int NT, typename Tin, typename Tout, bool VEC2>
-__global__ void __launch_bounds__(256) fcfs_fwd2d_tma(const __grid_constant__ TmaFwdParams T) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const FwdParams& P = T.P;
-    const AxisP& AY = P.ax[1];
-    const AxisP& AX = P.ax[2];
-    Tin* buf0 = reinterpret_cast<Tin*>(smem_raw);
-    Tin* buf1 = reinterpret_cast<Tin*>(smem_raw + T.buf_bytes);
-    float* sH = reinterpret_cast<float*>(smem_raw + 2 * T.buf_bytes);
-    float* sWx = sH + P.IR * P.OX;
-    float* sWy = sWx + AX.r * NT;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
-
-    // ---- per-thread constants of the x pass: one output column, G1 row groups
-    const int OX = P.OX, BW = T.BW;
-    const int G1 = blockDim.x / OX;
-    const int ox = threadIdx.x % OX, g1 = threadIdx.x / OX;
-    const int jx = ox % AX.r, ixl = ox / AX.r;
-    const bool x_active = g1 < G1;
-    const int xbase = ixl * AX.s + AX.off[jx];
-    // ---- per-thread constants of the y pass: VW columns, phase groups
-    constexpr int VW = VEC2 ? 2 : 1;
-    const int NCOL = OX / VW;
-    const int G2 = blockDim.x / NCOL;
-    const int cy = threadIdx.x % NCOL, g2 = threadIdx.x / NCOL;
-    const int oxy = cy * VW;
-    const bool y_active = g2 < G2;
-    const int Gw = max(1, G2 / AY.r);
-    const int npairs = AY.r * Gw;
-
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-
-    // each CTA owns a contiguous run of tiles (same plane for many tiles in a row)
-    const int ntiles = (int)T.ntiles;
-    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-    int tile = blockIdx.x * per;
-    const int tile_end = min(ntiles, tile + per);
-    if (tile >= tile_end) return;
-    if (threadIdx.x == 0) issue_tile<Tin>(T, tile_geo(T, tile), buf0, &bars[0]);
-    const bool learn = AX.learn || AY.learn;
-    int cur_c = -1;
-    float wxr[NT];
-    for (int k = 0; tile < tile_end; ++k, ++tile) {
-        const TileGeo geo = tile_geo(T, tile);
-        Tin* buf = (k & 1) ? buf1 : buf0;
-        // prefetch the next tile into the other buffer (its last reader passed the barrier below)
-        const int next = tile + 1;
-        if (threadIdx.x == 0 && next < tile_end)
-            issue_tile<Tin>(T, tile_geo(T, next), (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
-        const bool new_c = cur_c < 0 || (learn && geo.c != cur_c);
-        if (new_c) {  // per-channel (or fixed) taps
-            for (int e = threadIdx.x; e < AX.r * NT; e += blockDim.x) {
-                const int j = e / NT, t = e - j * NT;
-                sWx[e] = t < AX.nt_src ? (AX.learn ? AX.w[geo.c * AX.w_cstride + j * AX.nt_src + t] : AX.wf[j * AX.nt_src + t]) : 0.f;
-            }
-            for (int e = threadIdx.x; e < AY.r * NT; e += blockDim.x) {
-                const int j = e / NT, t = e - j * NT;
-                sWy[e] = t < AY.nt_src ? (AY.learn ? AY.w[geo.c * AY.w_cstride + j * AY.nt_src + t] : AY.wf[j * AY.nt_src + t]) : 0.f;
-            }
-            cur_c = geo.c;
-        }
-        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma);
-        __syncthreads();  // weights staged; TMA data visible to all
-        if (new_c) {
-#pragma unroll
-            for (int t = 0; t < NT; ++t) wxr[t] = sWx[jx * NT + t];
-        }
-        if (geo.edge) fix_edges<Tin>(T, geo, buf);
-
-        // ---- pass x: sH[ry][ox] for the tile's rows
-        if (x_active && ixl < geo.nwx) {
-            const Tin* src = buf + g1 * BW + geo.xoff + xbase;
-            float* dst = sH + g1 * OX + ox;
-            const int sstep = G1 * BW, dstep = G1 * OX;
-#pragma unroll 2
-            for (int ry = g1; ry < geo.rows; ry += G1) {
-                float acc = -0.f;
-#pragma unroll
-                for (int t = 0; t < NT; ++t) acc = fmaf(wxr[t], to_f<Tin>(src[t]), acc);
-                *dst = acc;
-                src += sstep;
-                dst += dstep;
-            }
-        }
-        __syncthreads();
-
-        // ---- pass y: thread = (VW columns, phase); outputs at pixel-shuffled positions
-        const int gox = geo.ix0 * AX.r + oxy;
-        const int nvalid = min(VW, AX.n_out - gox);
-        if (y_active && oxy / AX.r < geo.nwx && nvalid > 0) {
-            Tout* ybase = static_cast<Tout*>(P.y) + (long long)geo.plane * AY.n_out * AX.n_out + gox;
-            for (int p = g2; p < npairs; p += G2) {
-                const int jy = p % AY.r, wg = p / AY.r;
-                float w[NT];
-#pragma unroll
-                for (int t = 0; t < NT; ++t) w[t] = sWy[jy * NT + t];
-                int oy = (geo.iy0 + wg) * AY.r + jy;
-                const float* hp = sH + (wg * AY.s + AY.off[jy]) * OX + oxy;
-                int yoff = oy * AX.n_out;
-                const int hstep = Gw * AY.s * OX, ostep = Gw * AY.r, ystep = ostep * AX.n_out;
-                const int iend = geo.nwy;
-#pragma unroll 2
-                for (int iyl = wg; iyl < iend && oy < AY.n_out; iyl += Gw) {
-                    if (VEC2) {
-                        float a0 = -0.f, a1 = -0.f;
-#pragma unroll
-                        for (int t = 0; t < NT; ++t) {
-                            const float2 h = *reinterpret_cast<const float2*>(hp + t * OX);
-                            a0 = fmaf(w[t], h.x, a0);
-                            a1 = fmaf(w[t], h.y, a1);
-                        }
-                        if (nvalid == 2) store2(ybase + yoff, a0, a1);
-                        else ybase[yoff] = from_f<Tout>(a0);
-                    } else {
-                        float acc = -0.f;
-#pragma unroll
-                        for (int t = 0; t < NT; ++t) acc = fmaf(w[t], hp[t * OX], acc);
-                        ybase[yoff] = from_f<Tout>(acc);
-                    }
-                    hp += hstep;
-                    yoff += ystep;
-                    oy += ostep;
-                }
-            }
-        }
-        __syncthreads();  // sH and this buffer are free again
-    }
-}
-
-template <typename F>
-cudaError_t dispatch(int din, int dout, F&& f) {
-    if (din == FCFS_F32 && dout == FCFS_F32) return f((float*)nullptr, (float*)nullptr);
-    if (din == FCFS_BF16 && dout == FCFS_BF16) return f((__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr);
-    if (din == FCFS_F32 && dout == FCFS_BF16) return f((float*)nullptr, (__nv_bfloat16*)nullptr);
-    if (din == FCFS_BF16 && dout == FCFS_F32) return f((__nv_bfloat16*)nullptr, (float*)nullptr);
-    if (din == FCFS_U8 && dout == FCFS_F32) return f((uint8_t*)nullptr, (float*)nullptr);
-    if (din == FCFS_U8 && dout == FCFS_BF16) return f((uint8_t*)nullptr, (__nv_bfloat16*)nullptr);
+cudaError_t launch_forward_tma(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st) {
+    if (din == FCFS_F32) return launch_forward_tma_f32(T, nt, din, dout, st);
+    if (din == FCFS_BF16) return launch_forward_tma_bf16(T, nt, din, dout, st);
+    if (din == FCFS_U8) return launch_forward_tma_u8(T, nt, din, dout, st);
     return cudaErrorInvalidValue;
 }
 
-template <int NT, typename Tin, typename Tout>
-cudaError_t run(const TmaFwdParams& T, size_t smem, cudaStream_t st) {
-    const bool vec2 = (T.P.OX % 2 == 0) && (T.P.ax[2].n_out % 2 == 0) &&
-                      ((uintptr_t)T.P.y % (2 * sizeof(Tout)) == 0);
-    auto k = vec2 ? fcfs_fwd2d_tma<NT, Tin, Tout, true> : fcfs_fwd2d_tma<NT, Tin, Tout, false>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int threads = T.threads;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
-    k<<<(unsigned)grid, threads, smem, st>>>(T);
-    return cudaGetLastError();
+// Register-blocked variant: same phase count and window span on both axes,
+// interpolating taps (not the one-tap nearest copy), FP32 or BF16 storage.
+bool forward_rs_available(const TmaFwdParams& T, int din, int dout) {
+    const AxisP &AX = T.P.ax[2], &AY = T.P.ax[1];
+    if (din != dout || (din != FCFS_F32 && din != FCFS_BF16)) return false;
+    if (AX.r != AY.r || AX.span != AY.span || AX.nt_src < 2 || AY.nt_src < 2) return false;
+    if (T.P.OX % 2 || AX.n_out % 2) return false;
+    static const int pairs[][2] = {{2, 5}, {4, 6}, {3, 5}, {3, 3}, {5, 5}, {7, 8}};
+    for (auto& pr : pairs)
+        if (pr[0] == AX.r && pr[1] == AX.span) return true;
+    return false;
 }
 
-}  // namespace
-
-// Read (and clear) the status word of the bulk-copy kernels.
-int read_status_fwd_tma(int clear) {
-    int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_status_fwd_tma, sizeof(int)) != cudaSuccess) return -1;
-    if (clear && v) {
-        const int z = 0;
-        cudaMemcpyToSymbol(g_status_fwd_tma, &z, sizeof(int));
-    }
-    return v;
+cudaError_t launch_forward_rs(const TmaFwdParams& T, int din, cudaStream_t st) {
+    const int R = T.P.ax[2].r, span = T.P.ax[2].span;
+    return din == FCFS_F32 ? launch_forward_rs_f32(T, R, span, st) : launch_forward_rs_bf16(T, R, span, st);
 }
 
 size_t forward_tma_smem_bytes(const TmaFwdParams& T) { return (size_t)T.bar_off + 16; /* two mbarriers */ }
 
-#define FCFS_NT_CASES(X) X(1) X(2) X(3) X(4) X(5) X(7) X(9)
-
-cudaError_t launch_forward_tma(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st) {
-    const size_t smem = forward_tma_smem_bytes(T);
-    return dispatch(din, dout, [&](auto tin, auto tout) -> cudaError_t {
-        using Tin = std::remove_pointer_t<decltype(tin)>;
-        using Tout = std::remove_pointer_t<decltype(tout)>;
-        switch (nt) {
-#define CASE(N) \
-    case N: return run<N, Tin, Tout>(T, smem, st);
-            FCFS_NT_CASES(CASE)
-#undef CASE
-            default: return cudaErrorInvalidValue;
-        }
-    });
+// status words of the three translation units, or -1 if one cannot be read
+int read_status_fwd_tma(int clear) {
+    const int a = read_status_fwd_tma_f32(clear), b = read_status_fwd_tma_bf16(clear), c = read_status_fwd_tma_u8(clear);
+    if (a < 0 || b < 0 || c < 0) return -1;
+    return a | b | c;
 }
 
 }  // namespace fcfs

@@ -1,0 +1,341 @@
+// K1 (fast path, kernel templates): persistent, TMA-staged, double-buffered fused FCFS forward
+// for 1D/2D (Sec. 3.2 pseudocode; Sec. 4 with separable kernels).
+//
+// Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...  While it
+// computes tile k from one shared-memory buffer, the bulk-tensor copy of
+// tile k+1 lands in the other.  Per tile:
+//   stage   x~ tile (TMA box of the [planes][H][W] input; padding applied in
+//           shared memory on edge tiles: replicate/constant fix-up, reflect
+//           by a gather),
+//   pass x  sH[ry][ox] = sum_t Wx[jx][t] x~[ry][ixl*s_x + off_x[jx] + t]
+//           (thread = output column; its taps sit in registers),
+//   pass y  y[oy][ox]  = sum_t Wy[jy][t] sH[iyl*s_y + off_y[jy] + t][ox]
+//           (thread = output column and phase jy; taps in registers), stored
+//           at the pixel-shuffled position: the r-channel hidden layer is
+//           never written.
+// Accumulators start at -0.0 so a single tap of weight 1 (nearest) is an
+// exact copy, signed zeros included.
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+
+#include "fcfs_internal.cuh"
+#include "fcfs_tma.cuh"
+
+namespace fcfs {
+
+// Device status word of the bulk-copy forward kernels (bounded waits).  Each
+// translation unit that instantiates the kernels owns its copy.
+static __device__ int g_status_fwd_tma = 0;
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ float to_f(T v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float to_f<uint8_t>(uint8_t v) { return (float)v; }
+
+template <typename T>
+__device__ __forceinline__ T from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ uint8_t from_f<uint8_t>(float v) {
+    return (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg_raw(const T* p) { return *p; }
+
+struct TileGeo {
+    int plane, c, ix0, iy0, nwx, nwy, rows, cols, row0, col0, x_al, xoff;
+    bool edge;
+};
+
+// Tile index -> geometry, 32-bit arithmetic (the planner keeps the tile count
+// below 2^31).
+__device__ __forceinline__ TileGeo tile_geo(const TmaFwdParams& T, int tile) {
+    const FwdParams& P = T.P;
+    const AxisP& AY = P.ax[1];
+    const AxisP& AX = P.ax[2];
+    TileGeo g;
+    const int txy = P.tiles_x * P.tiles_y;
+    g.plane = tile / txy;
+    const int rem = tile - g.plane * txy;
+    const int ty = rem / P.tiles_x;
+    const int tx = rem - ty * P.tiles_x;
+    g.c = g.plane % P.C;
+    g.ix0 = tx * P.WX;
+    g.iy0 = ty * P.WY;
+    g.nwx = min(P.WX, AX.n_win - g.ix0);
+    g.nwy = min(P.WY, AY.n_win - g.iy0);
+    g.cols = (g.nwx - 1) * AX.s + AX.span;
+    g.rows = (g.nwy - 1) * AY.s + AY.span;
+    g.col0 = g.ix0 * AX.s + AX.lo;
+    g.row0 = g.iy0 * AY.s + AY.lo;
+    // innermost TMA coordinate rounded down to a 16-byte boundary
+    g.x_al = g.col0 >= 0 ? (g.col0 / T.align) * T.align : -(((-g.col0) + T.align - 1) / T.align) * T.align;
+    g.xoff = g.col0 - g.x_al;
+    g.edge = g.col0 < 0 || g.col0 + g.cols > AX.n_in || g.row0 < 0 || g.row0 + g.rows > AY.n_in;
+    return g;
+}
+
+template <typename Tin>
+__device__ __forceinline__ void issue_tile(const TmaFwdParams& T, const TileGeo& g, Tin* buf, uint64_t* bar) {
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, (uint32_t)(T.BW * T.BH * sizeof(Tin)));
+    tma_load_3d(buf, &T.tmap, g.x_al, g.row0, g.plane, bar);
+}
+
+// Padding on an edge tile, in shared memory.  Replicate and constant use the
+// in-tile samples the TMA box already holds; reflect (whose mirror may leave
+// the box) re-gathers the tile from global memory through the index map.
+template <typename Tin>
+__device__ __forceinline__ void fix_edges(const TmaFwdParams& T, const TileGeo& g, Tin* buf) {
+    const FwdParams& P = T.P;
+    const int H = P.ax[1].n_in, W = P.ax[2].n_in;
+    const int BW = T.BW;
+    if (P.pad == FCFS_PAD_REFLECT) {
+        const Tin* xp = static_cast<const Tin*>(P.x) + g.plane * (long long)H * W;
+        for (int e = threadIdx.x; e < g.rows * BW; e += blockDim.x) {
+            const int ry = e / BW, cx = e - ry * BW;
+            const int sy = ext_index(g.row0 + ry, H, P.pad);
+            const int sx = ext_index(g.x_al + cx, W, P.pad);
+            buf[ry * BW + cx] = ldg_raw(xp + (long long)sy * W + sx);
+        }
+        __syncthreads();
+        return;
+    }
+    const bool repl = P.pad == FCFS_PAD_REPLICATE;
+    const Tin cv = from_f<Tin>(P.padv);
+    // columns outside [0, W) on in-range rows
+    const int cl = max(0, -g.x_al);                 // box columns left of 0
+    const int cr = max(0, g.x_al + BW - W);         // box columns right of W-1
+    if (cl > 0 || cr > 0) {
+        const int ncol = cl + cr;
+        for (int e = threadIdx.x; e < g.rows * ncol; e += blockDim.x) {
+            const int ry = e / ncol, k = e - ry * ncol;
+            const int gy = g.row0 + ry;
+            if (gy < 0 || gy >= H) continue;
+            const int cx = k < cl ? k : BW - cr + (k - cl);
+            const int src = (k < cl ? 0 : W - 1) - g.x_al;
+            buf[ry * BW + cx] = repl ? buf[ry * BW + src] : cv;
+        }
+        __syncthreads();
+    }
+    // rows outside [0, H): copies of the edge rows, or the constant
+    const int rt = max(0, -g.row0), rb = max(0, g.row0 + g.rows - H);
+    if (rt > 0 || rb > 0) {
+        const int nrow = rt + rb;
+        for (int e = threadIdx.x; e < nrow * BW; e += blockDim.x) {
+            const int k = e / BW, cx = e - k * BW;
+            const int ry = k < rt ? k : g.rows - rb + (k - rt);
+            const int src = (k < rt ? 0 : H - 1) - g.row0;
+            buf[ry * BW + cx] = repl ? buf[src * BW + cx] : cv;
+        }
+        __syncthreads();
+    }
+}
+
+// Stores of n <= 4 adjacent outputs (the caller guarantees VW-element alignment).
+__device__ __forceinline__ void storev(float* p, const float* a, int n) {
+    if (n == 4) *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+    else if (n == 2) *reinterpret_cast<float2*>(p) = make_float2(a[0], a[1]);
+    else for (int i = 0; i < n; ++i) p[i] = a[i];
+}
+__device__ __forceinline__ void storev(__nv_bfloat16* p, const float* a, int n) {
+    if (n == 4) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(a[0], a[1]), hi = __floats2bfloat162_rn(a[2], a[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&lo);
+        u.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(p) = u;
+    } else if (n == 2) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a[0], a[1]);
+    } else {
+        for (int i = 0; i < n; ++i) p[i] = __float2bfloat16_rn(a[i]);
+    }
+}
+
+template <int VW>
+__device__ __forceinline__ void ldsv(const float* p, float* v) {
+    if (VW == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else if (VW == 2) {
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        v[0] = *p;
+    }
+}
+
+// VW: the y pass handles VW adjacent output columns per thread (VW-wide shared
+// loads and global stores); VW > 1 needs tile width and output row length
+// multiples of VW.  The CTA size (256 or 512 threads) is a plan parameter.
+template <int NT, typename Tin, typename Tout, int VW>
+__global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ TmaFwdParams T) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ TileGeo sgeo[2];
+    const FwdParams& P = T.P;
+    const AxisP& AY = P.ax[1];
+    const AxisP& AX = P.ax[2];
+    Tin* buf0 = reinterpret_cast<Tin*>(smem_raw);
+    Tin* buf1 = reinterpret_cast<Tin*>(smem_raw + T.buf_bytes);
+    float* sH = reinterpret_cast<float*>(smem_raw + 2 * T.buf_bytes);
+    float* sWx = sH + P.IR * P.OX;
+    float* sWy = sWx + AX.r * NT;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
+
+    // ---- per-thread constants of the x pass: one output column, G1 row groups
+    const int OX = P.OX, BW = T.BW;
+    const int G1 = blockDim.x / OX;
+    const int ox = threadIdx.x % OX, g1 = threadIdx.x / OX;
+    const int jx = ox % AX.r, ixl = ox / AX.r;
+    const bool x_active = g1 < G1;
+    const int xbase = ixl * AX.s + AX.off[jx];
+    // ---- per-thread constants of the y pass: VW columns, (phase, window group) pairs
+    const int NCOL = OX / VW;
+    const int G2 = blockDim.x / NCOL;
+    const int cy = threadIdx.x % NCOL, g2 = threadIdx.x / NCOL;
+    const int oxy = cy * VW;
+    const bool y_active = g2 < G2;
+    const int Gw = max(1, G2 / AY.r);
+    const int npairs = AY.r * Gw;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    // each CTA owns a contiguous run of tiles (same plane for many tiles in a row);
+    // thread 0 computes each tile's geometry once and shares it in shared memory
+    const int ntiles = (int)T.ntiles;
+    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+    int tile = blockIdx.x * per;
+    const int tile_end = min(ntiles, tile + per);
+    if (tile >= tile_end) return;
+    if (threadIdx.x == 0) {
+        sgeo[0] = tile_geo(T, tile);
+        issue_tile<Tin>(T, sgeo[0], buf0, &bars[0]);
+    }
+    const bool learn = AX.learn || AY.learn;
+    int cur_c = -1;
+    float wxr[NT];
+    for (int k = 0; tile < tile_end; ++k, ++tile) {
+        Tin* buf = (k & 1) ? buf1 : buf0;
+        // prefetch the next tile into the other buffer (its last reader passed the barrier below)
+        if (threadIdx.x == 0 && tile + 1 < tile_end) {
+            sgeo[(k + 1) & 1] = tile_geo(T, tile + 1);
+            issue_tile<Tin>(T, sgeo[(k + 1) & 1], (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
+        }
+        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma);
+        __syncthreads();  // TMA data and this tile's geometry visible to all
+        const TileGeo geo = sgeo[k & 1];
+        if (cur_c < 0 || (learn && geo.c != cur_c)) {  // per-channel (or fixed) taps
+            for (int e = threadIdx.x; e < AX.r * NT; e += blockDim.x) {
+                const int j = e / NT, t = e - j * NT;
+                sWx[e] = t < AX.nt_src ? (AX.learn ? AX.w[geo.c * AX.w_cstride + j * AX.nt_src + t] : AX.wf[j * AX.nt_src + t]) : 0.f;
+            }
+            for (int e = threadIdx.x; e < AY.r * NT; e += blockDim.x) {
+                const int j = e / NT, t = e - j * NT;
+                sWy[e] = t < AY.nt_src ? (AY.learn ? AY.w[geo.c * AY.w_cstride + j * AY.nt_src + t] : AY.wf[j * AY.nt_src + t]) : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < NT; ++t) wxr[t] = sWx[jx * NT + t];
+            cur_c = geo.c;
+        }
+        if (geo.edge) fix_edges<Tin>(T, geo, buf);
+
+        // ---- pass x: sH[ry][ox] for the tile's rows
+        if (x_active && ixl < geo.nwx) {
+            const Tin* src = buf + g1 * BW + geo.xoff + xbase;
+            float* dst = sH + g1 * OX + ox;
+            const int sstep = G1 * BW, dstep = G1 * OX;
+#pragma unroll 2
+            for (int ry = g1; ry < geo.rows; ry += G1) {
+                float acc = -0.f;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) acc = fmaf(wxr[t], to_f<Tin>(src[t]), acc);
+                *dst = acc;
+                src += sstep;
+                dst += dstep;
+            }
+        }
+        __syncthreads();
+
+        // ---- pass y: thread = (VW columns, phase); outputs at pixel-shuffled positions
+        const int gox = geo.ix0 * AX.r + oxy;
+        const int nvalid = min(VW, AX.n_out - gox);
+        if (y_active && oxy / AX.r < geo.nwx && nvalid > 0) {
+            Tout* ybase = static_cast<Tout*>(P.y) + (long long)geo.plane * AY.n_out * AX.n_out + gox;
+            for (int p = g2; p < npairs; p += G2) {
+                const int jy = p % AY.r, wg = p / AY.r;
+                float w[NT];
+#pragma unroll
+                for (int t = 0; t < NT; ++t) w[t] = sWy[jy * NT + t];
+                int oy = (geo.iy0 + wg) * AY.r + jy;
+                const float* hp = sH + (wg * AY.s + AY.off[jy]) * OX + oxy;
+                int yoff = oy * AX.n_out;
+                const int hstep = Gw * AY.s * OX, ostep = Gw * AY.r, ystep = ostep * AX.n_out;
+                const int iend = geo.nwy;
+#pragma unroll 2
+                for (int iyl = wg; iyl < iend && oy < AY.n_out; iyl += Gw) {
+                    float acc[VW];
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) acc[v] = -0.f;
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) {
+                        float h[VW];
+                        ldsv<VW>(hp + t * OX, h);
+#pragma unroll
+                        for (int v = 0; v < VW; ++v) acc[v] = fmaf(w[t], h[v], acc[v]);
+                    }
+                    storev(ybase + yoff, acc, nvalid);
+                    hp += hstep;
+                    yoff += ystep;
+                    oy += ostep;
+                }
+            }
+        }
+        __syncthreads();  // sH and this buffer are free again
+    }
+}
+
+template <int NT, typename Tin, typename Tout>
+cudaError_t run(const TmaFwdParams& T, size_t smem, cudaStream_t st) {
+    const int no = T.P.ax[2].n_out;
+    const uintptr_t y = (uintptr_t)T.P.y;
+    const bool v4 = T.P.OX % 4 == 0 && no % 4 == 0 && y % (4 * sizeof(Tout)) == 0;
+    const bool v2 = T.P.OX % 2 == 0 && no % 2 == 0 && y % (2 * sizeof(Tout)) == 0;
+    auto k = v4 ? fcfs_fwd2d_tma<NT, Tin, Tout, 4> : v2 ? fcfs_fwd2d_tma<NT, Tin, Tout, 2> : fcfs_fwd2d_tma<NT, Tin, Tout, 1>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int threads = T.threads;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
+    k<<<(unsigned)grid, threads, smem, st>>>(T);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace fcfs

@@ -1009,7 +1009,7 @@ TileChoice default_tma_tiles(const FwdParams& P0, int es) {
     return t;
 }
 
-int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T) {
+int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T, int threads) {
     memset(T, 0, sizeof(*T));
     T->P = P;
     const int es = dtype_size(d->dtype_in);
@@ -1019,7 +1019,8 @@ int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T) {
     if (P.OX > 256) return fail(FCFS_ERR_UNSUPPORTED, "tile wider than the CTA");
     T->ntiles = (long long)P.tiles_x * P.tiles_y * P.planes;
     if (T->ntiles >= (1LL << 31)) return fail(FCFS_ERR_UNSUPPORTED, "too many tiles");
-    T->threads = 256;
+    T->threads = threads > 0 ? threads : 256;
+    if (P.OX > T->threads) return fail(FCFS_ERR_UNSUPPORTED, "tile wider than the CTA");
     const cuuint64_t W = (cuuint64_t)P.ax[2].n_in, H = (cuuint64_t)P.ax[1].n_in;
     cuuint64_t dims[3] = {W, H, (cuuint64_t)P.planes};
     cuuint64_t strides[2] = {W * es, W * H * es};
@@ -1042,8 +1043,13 @@ int launch_choice(const fcfs_desc* d, FwdParams& P, int ntk, const TileChoice& t
     if (t.tma == 1 && !is3d && tma_eligible(d, P.x)) {
         apply_tiles(P, false, t.WX, t.WY, 1, t.G);
         TmaFwdParams T;
-        int rc = prepare_tma(d, P, &T);
-        if (rc == FCFS_OK && forward_tma_smem_bytes(T) <= 227 * 1024) {
+        int rc = prepare_tma(d, P, &T, t.threads);
+        if (rc == FCFS_OK && forward_tma_smem_bytes(T) <= 200 * 1024) {
+            if (t.rs != 0 && forward_rs_available(T, d->dtype_in, d->dtype_out)) {
+                cudaError_t e = launch_forward_rs(T, d->dtype_in, st);
+                if (e == cudaSuccess) return FCFS_OK;
+                if (e != cudaErrorInvalidValue) return cuda_fail(e, "forward (register-blocked) launch");
+            }
             cudaError_t e = launch_forward_tma(T, ntk, d->dtype_in, d->dtype_out, st);
             return e == cudaSuccess ? FCFS_OK : cuda_fail(e, "forward (bulk-copy) launch");
         }

@@ -11,6 +11,8 @@ struct TileChoice {
     int WX, WY, WD;  // windows per tile along x, y, depth
     int G = 0;       // thread groups per output column (0: planner default)
     int tma = -1;    // 1: TMA-staged persistent kernel, 0: gather kernel, -1: best available
+    int threads = 0; // CTA size of the TMA-staged kernel (0: 256)
+    int rs = 1;      // 1: register-blocked variant when one is compiled for (r, span), 0: per-output kernel
 };
 
 int fail(int status, const char* fmt, ...);
@@ -36,7 +38,7 @@ void identity_axis(AxisP* A, int nt_kernel);
 int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* out, int* ntk);
 void apply_tiles(FwdParams& P, bool is3d, int WX, int WY, int WD, int G = 0);
 bool tma_eligible(const fcfs_desc* d, const void* x);
-int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T);
+int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T, int threads = 256);
 TileChoice default_tma_tiles(const FwdParams& P, int es);
 int launch_choice(const fcfs_desc* d, FwdParams& P, int ntk, const TileChoice& t, cudaStream_t st);
 TileChoice default_tiles(const FwdParams& P, bool is3d);

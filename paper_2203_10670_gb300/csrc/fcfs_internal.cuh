@@ -257,6 +257,8 @@ cudaError_t launch_forward_3d(const FwdParams& P, int nt, int din, int dout, cud
 cudaError_t launch_nearest(const NearestParams& P, int din, int dout, cudaStream_t st);
 cudaError_t launch_forward_tma(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st);
 size_t forward_tma_smem_bytes(const TmaFwdParams& T);
+bool forward_rs_available(const TmaFwdParams& T, int din, int dout);
+cudaError_t launch_forward_rs(const TmaFwdParams& T, int din, cudaStream_t st);
 int read_status_fwd_tma(int clear);
 int read_status_bwd_tma(int clear);
 cudaError_t launch_dx_tma(const TmaDxParams& T, int nt, int dg, int dx, cudaStream_t st);

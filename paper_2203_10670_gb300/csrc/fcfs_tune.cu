@@ -41,16 +41,20 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     const int ry = P0.ax[1].r;
     for (int oxt : ox_targets)
         for (int oyt : oy_targets)
-            for (int gm = 0; gm < 2; ++gm) {
+            for (int gm = 0; gm < 4; ++gm) {
                 TileChoice t{std::max(1, oxt / P0.ax[2].r), std::max(1, oyt / ry), def.WD};
                 t.tma = def.tma;
-                t.G = gm == 0 ? def.G : (def.G == ry ? 1 : ry);
+                // TMA kernel: the second variant is the 512-thread CTA; gather kernel: thread groups
+                t.G = tma ? 0 : (gm == 0 ? def.G : (def.G == ry ? 1 : ry));
+                t.threads = tma ? ((gm & 1) == 0 ? 256 : 512) : 0;
+                t.rs = gm < 2 ? 1 : 0;
+                if (!tma && gm >= 2) continue;
                 FwdParams P = P0;
                 apply_tiles(P, is3d, t.WX, t.WY, t.WD, t.G);
-                if (P.OX * P.G > 512) continue;
+                if (!tma && P.OX * P.G > 512) continue;
                 if (tma) {
                     TmaFwdParams T;
-                    if (prepare_tma(d, P, &T) != FCFS_OK || forward_tma_smem_bytes(T) > 200 * 1024) {
+                    if (prepare_tma(d, P, &T, t.threads) != FCFS_OK || forward_tma_smem_bytes(T) > 200 * 1024) {
                         clear_error();
                         continue;
                     }
@@ -59,9 +63,11 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
                 }
                 t.WX = P.WX;
                 t.WY = P.WY;
-                t.G = P.G;
+                t.G = tma ? 0 : P.G;
                 bool dup = false;
-                for (auto& c : cands) dup |= (c.WX == t.WX && c.WY == t.WY && c.G == t.G && c.tma == t.tma);
+                for (auto& c : cands)
+                    dup |= (c.WX == t.WX && c.WY == t.WY && c.G == t.G && c.tma == t.tma && c.threads == t.threads &&
+                            c.rs == t.rs);
                 if (!dup) cands.push_back(t);
             }
     cudaEvent_t e0, e1;
