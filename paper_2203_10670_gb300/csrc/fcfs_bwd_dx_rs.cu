@@ -1,0 +1,255 @@
+// K4, register-blocked variant: the input gradient with both adjoint passes
+// working per adjoint window (compile-time phase count S = s and window span
+// SPAN, the same on both axes).  A thread loads the SPAN samples an adjoint
+// window reads once and produces all S outputs from span-wide zero-padded
+// weight rows WF[u][k] held in registers.  Intermediate columns are indexed
+// relative to the tile's first adjoint window, so whole windows are written
+// without bounds tests; edge tiles fold the virtual indices as the
+// per-output kernel does.
+#include "fcfs_bwd_tma.cuh"
+
+namespace fcfs {
+namespace {
+
+// span-wide adjoint weight rows of one axis for channel c
+template <int S, int SPAN>
+__device__ __forceinline__ void stage_adj_span(float* WF, const AxisP& A, const AdjP& J, int c) {
+    for (int e = threadIdx.x; e < S * SPAN; e += blockDim.x) {
+        const int u = e / SPAN, k = e - u * SPAN;
+        const int t = k - J.off[u];
+        float v = 0.f;
+        if (t >= 0 && t < J.ntu[u]) {
+            const int f = J.idx[u * kMaxAdjTaps + t];
+            if (f >= 0) v = fwd_weight(A, c, f);
+        }
+        WF[e] = v;
+    }
+}
+
+// XSPEC: one adjoint window per thread in the x pass (lanes stride r samples:
+// bank-conflict free for odd r); otherwise one intermediate column per thread.
+template <int S, int SPAN, typename Tg, typename Tx, bool XSPEC>
+__global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ float sWFx[S * SPAN], sWFy[S * SPAN];
+    const AdjP& JX = T.aj[2];
+    const AdjP& JY = T.aj[1];
+    unsigned char* bufs[2] = {smem_raw, smem_raw + T.buf_bytes};
+    float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
+    const int QX = T.QX, GBW = T.GBW, FXP = T.FXP, R = JX.r;
+    const int Nx = JX.n_x, Ny = JY.n_x;
+    // x pass mapping
+    const int XT = XSPEC ? T.WAcap : T.WAcap * S;
+    const int G1 = blockDim.x / XT;
+    const int xi = threadIdx.x % XT, g1 = threadIdx.x / XT;
+    // y pass mapping
+    const int G2 = blockDim.x / QX;
+    const int cl = threadIdx.x % QX, g2 = threadIdx.x / QX;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int ntiles = (int)T.ntiles;
+    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+    int tile = blockIdx.x * per;
+    const int tile_end = min(ntiles, tile + per);
+    if (tile >= tile_end) return;
+    if (threadIdx.x == 0) issue<Tg>(T, dx_geo(T, tile), bufs[0], &bars[0]);
+    const bool learn = T.ax[2].learn || T.ax[1].learn;
+    int cur_c = -1;
+    for (int k = 0; tile < tile_end; ++k, ++tile) {
+        const DxGeo geo = dx_geo(T, tile);
+        const Tg* G0 = reinterpret_cast<const Tg*>(bufs[k & 1]);
+        if (threadIdx.x == 0 && tile + 1 < tile_end)
+            issue<Tg>(T, dx_geo(T, tile + 1), bufs[(k + 1) & 1], &bars[(k + 1) & 1]);
+        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        if (cur_c < 0 || (learn && geo.c != cur_c)) {
+            stage_adj_span<S, SPAN>(sWFx, T.ax[2], JX, geo.c);
+            stage_adj_span<S, SPAN>(sWFy, T.ax[1], JY, geo.c);
+            cur_c = geo.c;
+        }
+        __syncthreads();
+
+        const int nAX = geo.X.ahi >= geo.X.alo ? geo.X.ahi - geo.X.alo + 1 : 0;
+        const int nAY = geo.Y.ahi >= geo.Y.alo ? geo.Y.ahi - geo.Y.alo + 1 : 0;
+        const int nGR = nAY ? (nAY - 1) * R + SPAN : 0;
+        const int fxb = geo.X.alo * S + JX.lo_out;  // extended index of intermediate column 0
+        // ---- pass x (adjoint along x) for every staged g row
+        if (g1 < G1) {
+            if (XSPEC) {
+                if (xi < nAX) {
+                    float wf[S][SPAN];
+#pragma unroll
+                    for (int u = 0; u < S; ++u)
+#pragma unroll
+                        for (int q = 0; q < SPAN; ++q) wf[u][q] = sWFx[u * SPAN + q];
+                    const Tg* src = G0 + g1 * GBW + geo.xoff + xi * R;
+                    float* dst = sF + g1 * FXP + xi * S;
+                    for (int gr = g1; gr < nGR; gr += G1) {
+                        float v[SPAN];
+#pragma unroll
+                        for (int q = 0; q < SPAN; ++q) v[q] = to_f<Tg>(src[q]);
+#pragma unroll
+                        for (int u = 0; u < S; ++u) {
+                            float acc = 0.f;
+#pragma unroll
+                            for (int q = 0; q < SPAN; ++q) acc = fmaf(wf[u][q], v[q], acc);
+                            dst[u] = acc;
+                        }
+                        src += G1 * GBW;
+                        dst += G1 * FXP;
+                    }
+                }
+            } else {
+                const int aw = xi / S, u = xi - aw * S;
+                if (aw < nAX) {
+                    float wf[SPAN];
+#pragma unroll
+                    for (int q = 0; q < SPAN; ++q) wf[q] = sWFx[u * SPAN + q];
+                    const Tg* src = G0 + g1 * GBW + geo.xoff + aw * R;
+                    float* dst = sF + g1 * FXP + xi;
+                    for (int gr = g1; gr < nGR; gr += G1) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int q = 0; q < SPAN; ++q) acc = fmaf(wf[q], to_f<Tg>(src[q]), acc);
+                        *dst = acc;
+                        src += G1 * GBW;
+                        dst += G1 * FXP;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // ---- fold x: virtual columns onto the real column the padding maps them to
+        if (geo.X.left || geo.X.right) {
+            for (int gr = threadIdx.x; gr < nGR; gr += blockDim.x) {
+                float* row = sF + gr * FXP;
+                const int l1 = min(geo.X.vhi, -1), r0 = max(geo.X.vlo, Nx);
+                for (int v = geo.X.vlo; v <= l1; ++v) {
+                    const int q = ext_index(v, Nx, T.pad);
+                    if (q >= geo.qx0 && q < geo.qx0 + geo.nqx) row[q - fxb] += row[v - fxb];
+                }
+                for (int v = r0; v <= geo.X.vhi; ++v) {
+                    const int q = ext_index(v, Nx, T.pad);
+                    if (q >= geo.qx0 && q < geo.qx0 + geo.nqx) row[q - fxb] += row[v - fxb];
+                }
+            }
+            __syncthreads();
+        }
+        // ---- pass y (adjoint along y) on the tile's real columns
+        const bool ypath_smem = geo.Y.left || geo.Y.right || !geo.Y.covered;
+        float* sO = reinterpret_cast<float*>(bufs[k & 1]);  // the g tile is consumed
+        const int q = geo.qx0 + cl;
+        const bool col_ok = g2 < G2 && cl < geo.nqx;
+        const bool col_has = col_ok && q <= geo.X.vhi;
+        Tx* xcol = static_cast<Tx*>(T.gx) + (long long)geo.plane * Ny * Nx + q;
+        if (col_ok) {
+            float wf[S][SPAN];
+#pragma unroll
+            for (int u = 0; u < S; ++u)
+#pragma unroll
+                for (int qq = 0; qq < SPAN; ++qq) wf[u][qq] = sWFy[u * SPAN + qq];
+            const int fcol = q - fxb;
+            for (int ay = g2; ay < nAY; ay += G2) {
+                float v[SPAN];
+                if (col_has) {
+                    const float* src = sF + ay * R * FXP + fcol;
+#pragma unroll
+                    for (int qq = 0; qq < SPAN; ++qq) v[qq] = src[qq * FXP];
+                } else {
+#pragma unroll
+                    for (int qq = 0; qq < SPAN; ++qq) v[qq] = 0.f;
+                }
+                const int vb = (geo.Y.alo + ay) * S + JY.lo_out;
+#pragma unroll
+                for (int u = 0; u < S; ++u) {
+                    const int vr = vb + u;
+                    if (vr < geo.Y.vlo || vr > geo.Y.vhi) continue;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int qq = 0; qq < SPAN; ++qq) acc = fmaf(wf[u][qq], v[qq], acc);
+                    if (ypath_smem) sO[(vr - geo.Y.vlo) * QX + cl] = acc;
+                    else store_out(xcol + (long long)vr * Nx, acc);
+                }
+            }
+        }
+        if (ypath_smem) {
+            __syncthreads();
+            if (col_ok) {
+                for (int qy = geo.qy0 + g2; qy < geo.qy0 + geo.nqy; qy += G2) {
+                    float acc = (qy >= geo.Y.vlo && qy <= geo.Y.vhi) ? sO[(qy - geo.Y.vlo) * QX + cl] : 0.f;
+                    if (geo.Y.left || geo.Y.right) {
+                        const int l1 = min(geo.Y.vhi, -1), r0 = max(geo.Y.vlo, Ny);
+                        for (int v = geo.Y.vlo; v <= l1; ++v)
+                            if (ext_index(v, Ny, T.pad) == qy) acc += sO[(v - geo.Y.vlo) * QX + cl];
+                        for (int v = r0; v <= geo.Y.vhi; ++v)
+                            if (ext_index(v, Ny, T.pad) == qy) acc += sO[(v - geo.Y.vlo) * QX + cl];
+                    }
+                    store_out(xcol + (long long)qy * Nx, acc);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int S, int SPAN, typename Tg>
+cudaError_t run_rs(const TmaDxParams& T, cudaStream_t st) {
+    const size_t smem = (size_t)T.bar_off + 16;
+    // measured: the variant pays off when the x pass can own whole windows
+    // (odd r, bank-conflict free) and the weight rows stay small; otherwise
+    // the per-output kernel is faster
+    const bool xs = (T.aj[2].r % 2) == 1;
+    if (!xs || S * SPAN > 40) return cudaErrorInvalidValue;
+    auto k = fcfs_bwd_dx2d_rs<S, SPAN, Tg, Tg, true>;
+    if (T.WAcap > T.threads) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
+    k<<<(unsigned)grid, T.threads, smem, st>>>(T);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define FCFS_DX_RS_PAIRS(X) X(4, 10) X(2, 7) X(2, 4) X(3, 4)
+
+bool dx_rs_compiled(int S, int span) {
+#define CASE(a, b) \
+    if (S == a && span == b) return true;
+    FCFS_DX_RS_PAIRS(CASE)
+#undef CASE
+    return false;
+}
+
+cudaError_t launch_dx_rs(const TmaDxParams& T, int dt, cudaStream_t st) {
+    const int S = T.aj[2].s, span = T.rs_span;
+#define CASE(a, b)                                                                              \
+    if (S == a && span == b)                                                                    \
+        return dt == FCFS_F32 ? run_rs<a, b, float>(T, st) : run_rs<a, b, __nv_bfloat16>(T, st);
+    FCFS_DX_RS_PAIRS(CASE)
+#undef CASE
+    return cudaErrorInvalidValue;
+}
+
+int read_status_bwd_rs(int clear) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_status_bwd_tma, sizeof(int)) != cudaSuccess) return -1;
+    if (clear && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_status_bwd_tma, &z, sizeof(int));
+    }
+    return v;
+}
+
+}  // namespace fcfs

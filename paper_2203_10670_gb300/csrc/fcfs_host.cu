@@ -2,6 +2,7 @@
 // and geometry tables of Sec. 3.2 / Sec. 5.2, and the tile planner.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -669,14 +670,28 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
     const int Nx = T->aj[2].n_x, Ny = T->aj[1].n_x;
     T->QX = Nx >= 128 ? 128 : Nx > 64 ? 128 : Nx > 32 ? 64 : 32;
     T->QY = std::min(32, std::max(1, Ny));
+    // register-blocked variant: one phase count and window span on both axes
+    auto true_span = [](const AdjP& J) {
+        int sp = 0;
+        for (int u = 0; u < J.s; ++u) sp = std::max(sp, J.off[u] + J.ntu[u]);
+        return sp;
+    };
+    const bool rs_ok = T->aj[2].s == T->aj[1].s && T->aj[2].r == T->aj[1].r &&
+                       true_span(T->aj[2]) == true_span(T->aj[1]) && dx_rs_compiled(T->aj[2].s, true_span(T->aj[2]));
+    T->rs_span = rs_ok ? true_span(T->aj[2]) : 0;
     for (int it = 0; it < 8; ++it) {
         // capacities over every tile position of each axis
-        int vx = 1, vy = 1, gw = 1, gh = 1;
+        int vx = 1, vy = 1, gw = 1, gh = 1, wa = 1;
         for (int q0 = 0; q0 < Nx; q0 += T->QX) {
             const AxRange R = ax_range(T->aj[2], d->pad, q0, std::min(Nx, q0 + T->QX) - 1);
             vx = std::max(vx, R.vhi - R.vlo + 1);
-            if (R.ahi >= R.alo) gw = std::max(gw, (R.ahi - R.alo) * T->aj[2].r + T->aj[2].span);
+            if (R.ahi >= R.alo) {
+                gw = std::max(gw, (R.ahi - R.alo) * T->aj[2].r + T->aj[2].span);
+                wa = std::max(wa, R.ahi - R.alo + 1);
+            }
         }
+        T->WAcap = wa;
+        T->FXP = std::max(vx, wa * T->aj[2].s);
         for (int q0 = 0; q0 < Ny; q0 += T->QY) {
             const AxRange R = ax_range(T->aj[1], d->pad, q0, std::min(Ny, q0 + T->QY) - 1);
             vy = std::max(vy, R.vhi - R.vlo + 1);
@@ -690,7 +705,7 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
         const size_t obytes = (size_t)T->VYcap * T->QX * 4;
         T->buf_bytes = (int)((std::max(gbytes, obytes) + 127) / 128 * 128);
         T->fx_off = 2 * T->buf_bytes;
-        T->w_off = T->fx_off + T->GBH * T->VXcap * 4;
+        T->w_off = T->fx_off + T->GBH * T->FXP * 4;
         T->bar_off = (T->w_off + (T->aj[2].s + T->aj[1].s) * w * 4 + 15) / 16 * 16;
         if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 16 <= 56 * 1024) break;
         if (T->QX > 64 && T->QX >= 4 * T->QY) T->QX /= 2;
@@ -899,7 +914,9 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
         TmaDxParams T;
         int ntd = 0;
         if (plan_dx_tma(d, B, gy, gx, &T, &ntd) == FCFS_OK) {
-            cudaError_t e = launch_dx_tma(T, ntd, d->dtype_out, d->dtype_in, st);
+            cudaError_t e = cudaErrorInvalidValue;
+            if (T.rs_span > 0) e = launch_dx_rs(T, d->dtype_out, st);
+            if (e == cudaErrorInvalidValue) e = launch_dx_tma(T, ntd, d->dtype_out, d->dtype_in, st);
             if (e != cudaSuccess) return cuda_fail(e, "input-gradient (bulk-copy) launch");
             gx = nullptr;  // done
         }

@@ -139,6 +139,9 @@ struct TmaDxParams {
     long long ntiles;
     const void* gy;
     void* gx;
+    // register-blocked variant: span every adjoint window reads (same on both
+    // axes), adjoint windows per tile row, pitch of the window-relative Fx
+    int rs_span, WAcap, FXP;
 };
 
 // Bulk-copy staged weight-gradient parameters (1D/2D): forward tile
@@ -262,6 +265,8 @@ cudaError_t launch_forward_rs(const TmaFwdParams& T, int din, cudaStream_t st);
 int read_status_fwd_tma(int clear);
 int read_status_bwd_tma(int clear);
 cudaError_t launch_dx_tma(const TmaDxParams& T, int nt, int dg, int dx, cudaStream_t st);
+cudaError_t launch_dx_rs(const TmaDxParams& T, int dt, cudaStream_t st);
+bool dx_rs_compiled(int S, int span);
 cudaError_t launch_dw_tma(const TmaDwParams& T, int nt, int dt, cudaStream_t st, const void* x);
 size_t forward_smem_bytes(const FwdParams& P, bool is3d);
 size_t dx_smem_bytes(const BwdParams& P, bool is3d);
