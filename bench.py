@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--backward-only", action="store_true",
                    help="time only a backward: the c3 layer (bf16, 5/4 learnable) or, with --only, the "
                         "input gradient of that c2 op (fp32), with --batch images")
+    p.add_argument("--volume", action="store_true",
+                   help="time only the c5 volume (1x1x256^3 fp32, trilinear 3/2): forward and input gradient")
     return p.parse_args()
 
 
@@ -315,12 +317,12 @@ def run_ours(args, rank, world, device):
         line["cpu_baseline"] = {"value": pix / cs / 1e9, "unit": "Gpix/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
     if not args.no_extras:
-        line["extras"] = extras(fcfs, inputs, device, stream, peak)
+        line["extras"] = extras(fcfs, inputs, device, stream, peak, tune=not args.no_tune)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def extras(fcfs, inputs, device, stream, peak):
+def extras(fcfs, inputs, device, stream, peak, tune=True):
     """BF16 storage of the same ops, the differentiable BF16 layer (c3) and the large configs (c5)."""
     out = {}
     steps = 5
@@ -375,6 +377,9 @@ def extras(fcfs, inputs, device, stream, peak):
         ax = [fcfs.Axis(r, s, m)] * axes_n
         x5 = inputs.uniform(spec["shape"], spec["seed"], device=device)
         y5 = fcfs.resize(x5, ax)
+        if tune:
+            d5 = fcfs.make_desc(x5.shape, ax, 0, 0)
+            fcfs.fcfs_tune_forward(d5, x5.data_ptr(), y5.data_ptr(), stream.cuda_stream, 3)
         t = timed(lambda: fcfs.resize(x5, ax, out=y5), steps, stream) / steps
         tdx = timed(lambda: fcfs.resize_backward(None, y5, ax, in_shape=tuple(x5.shape), in_dtype=x5.dtype),
                     steps, stream) / steps
@@ -468,6 +473,34 @@ def backward_only(args, device):
     print(json.dumps({"mode": "c3 backward", "batch": args.batch, "ms": t / args.steps * 1e3}), flush=True)
 
 
+def volume_only(args, device):
+    """c5 volume alone: forward and input gradient of the 256^3 trilinear 3/2 resize, for profiling."""
+    from paper_2203_10670_gb300 import build as B
+
+    B.build()
+    from paper_2203_10670_gb300 import fcfs, inputs
+
+    stream = torch.cuda.current_stream(device)
+    spec = inputs.C5_3D
+    ax = [fcfs.Axis(*spec["ratio"], fcfs.BILINEAR)] * 3
+    x = inputs.uniform(spec["shape"], spec["seed"], device=device)
+    y = fcfs.resize(x, ax)
+    if not args.no_tune:
+        d = fcfs.make_desc(x.shape, ax, 0, 0)
+        fcfs.fcfs_tune_forward(d, x.data_ptr(), y.data_ptr(), stream.cuda_stream, 3)
+
+    def bwd():
+        fcfs.resize_backward(None, y, ax, in_shape=tuple(x.shape), in_dtype=x.dtype)
+
+    for _ in range(max(1, args.warmup)):
+        fcfs.resize(x, ax, out=y)
+        bwd()
+    tf = timed(lambda: fcfs.resize(x, ax, out=y), args.steps, stream)
+    tb = timed(bwd, args.steps, stream)
+    print(json.dumps({"mode": "c5 volume 256^3 trilinear 3/2 fp32", "fwd_ms": tf / args.steps * 1e3,
+                      "bwd_dx_ms": tb / args.steps * 1e3}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -483,6 +516,9 @@ def main():
     try:
         if args.backward_only:
             backward_only(args, device)
+            return
+        if args.volume:
+            volume_only(args, device)
             return
         run_ours(args, rank, world, device)
     finally:

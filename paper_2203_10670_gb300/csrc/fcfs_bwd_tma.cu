@@ -188,17 +188,18 @@ cudaError_t run(const TmaDxParams& T, cudaStream_t st) {
 }  // namespace
 
 int read_status_bwd_rs(int clear);
+int read_status_bwd_dx3d(int clear);
 
 int read_status_bwd_tma(int clear) {
-    const int w = read_status_bwd_rs(clear);
-    if (w < 0) return -1;
+    const int w = read_status_bwd_rs(clear), w3 = read_status_bwd_dx3d(clear);
+    if (w < 0 || w3 < 0) return -1;
     int v = 0;
     if (cudaMemcpyFromSymbol(&v, g_status_bwd_tma, sizeof(int)) != cudaSuccess) return -1;
     if (clear && v) {
         const int z = 0;
         cudaMemcpyToSymbol(g_status_bwd_tma, &z, sizeof(int));
     }
-    return v | w;
+    return v | w | w3;
 }
 
 #define FCFS_ADJ_NT_CASES(X) X(2) X(3) X(4) X(6) X(8) X(10) X(12) X(16)

@@ -11,6 +11,8 @@ cudaError_t launch_forward_rs_bf16(const TmaFwdParams& T, int R, int span, cudaS
 int read_status_fwd_tma_f32(int clear);
 int read_status_fwd_tma_bf16(int clear);
 int read_status_fwd_tma_u8(int clear);
+int read_status_fwd3d(int clear);
+int read_status_fwd3d_rs(int clear);
 
 cudaError_t launch_forward_tma(const TmaFwdParams& T, int nt, int din, int dout, cudaStream_t st) {
     if (din == FCFS_F32) return launch_forward_tma_f32(T, nt, din, dout, st);
@@ -39,11 +41,12 @@ cudaError_t launch_forward_rs(const TmaFwdParams& T, int din, cudaStream_t st) {
 
 size_t forward_tma_smem_bytes(const TmaFwdParams& T) { return (size_t)T.bar_off + 16; /* two mbarriers */ }
 
-// status words of the three translation units, or -1 if one cannot be read
+// status words of the bulk-copy forward translation units, or -1 if one cannot be read
 int read_status_fwd_tma(int clear) {
     const int a = read_status_fwd_tma_f32(clear), b = read_status_fwd_tma_bf16(clear), c = read_status_fwd_tma_u8(clear);
-    if (a < 0 || b < 0 || c < 0) return -1;
-    return a | b | c;
+    const int e = read_status_fwd3d(clear), f = read_status_fwd3d_rs(clear);
+    if (a < 0 || b < 0 || c < 0 || e < 0 || f < 0) return -1;
+    return a | b | c | e | f;
 }
 
 }  // namespace fcfs

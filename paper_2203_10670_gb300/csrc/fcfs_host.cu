@@ -416,8 +416,8 @@ int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
     TileChoice tc;
     const bool have = get_plan(P, d->ndim, d->dtype_in, d->dtype_out, &tc);
     if (!have) {
-        const bool use_tma = d->ndim <= 2 && tma_eligible(d, x);
-        tc = use_tma ? default_tma_tiles(P, dtype_size(d->dtype_in)) : default_tiles(P, d->ndim == 3);
+        const bool use_tma = tma_eligible(d, x);
+        tc = use_tma ? default_tma_tiles(P, dtype_size(d->dtype_in), d->ndim == 3) : default_tiles(P, d->ndim == 3);
         tc.tma = use_tma ? 1 : 0;
     }
     return launch_choice(d, P, ntk, tc, st);
@@ -736,6 +736,122 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
     return FCFS_OK;
 }
 
+// Plan the bulk-copy 3D input-gradient kernel (same storage type for g and
+// dx, 16-byte row pitch of g, adjoint taps within the kernel templates).
+// Tiles of 64 (or 32) x 16 real (x, y) indices and a depth chunk sized so the
+// persistent grid gets several tiles per CTA.
+static int plan_dx3_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, void* gx, TmaDx3Params* T,
+                        int* ntk) {
+    if (d->ndim != 3 || d->dtype_in != d->dtype_out || d->dtype_in == FCFS_U8) return -1;
+    const int es = dtype_size(d->dtype_out);
+    const long long Wo = d->out_shape[2];
+    if (((uintptr_t)gy) % 16 || (Wo * es) % 16) return -1;
+    if (d->n * d->c >= (1LL << 31)) return -1;
+    memset(T, 0, sizeof(*T));
+    int nt = 1;
+    for (int a = 0; a < 3; ++a) {
+        T->ax[a] = B.ax[a];
+        const int n = build_adjp(B.ax[a], &T->aj[a]);
+        if (n < 0) return -1;
+        nt = std::max(nt, n);
+    }
+    const int w = adj_template_taps(nt);
+    if (w < 0 || w > 8) return -1;
+    for (int a = 0; a < 3; ++a) {
+        AdjP& J = T->aj[a];
+        J.nt = w;
+        int span = 0;
+        for (int u = 0; u < J.s; ++u) span = std::max(span, J.off[u] + w);
+        J.span = span;
+    }
+    T->C = (int)d->c;
+    T->pad = d->pad;
+    T->align = 16 / es;
+    T->threads = 256;
+    // depth indices that receive folded padding contributions
+    const AdjP& JD = T->aj[0];
+    const int Nd = JD.n_x, Ny = T->aj[1].n_x, Nx = T->aj[2].n_x;
+    T->nL = T->nR = 0;
+    if (d->pad != FCFS_PAD_CONSTANT) {
+        for (int v = JD.vmin; v < 0; ++v) T->nL = std::max(T->nL, ext_index(v, Nd, d->pad) + 1);
+        int tmin = Nd;
+        for (int v = Nd; v <= JD.vmax; ++v) tmin = std::min(tmin, ext_index(v, Nd, d->pad));
+        T->nR = Nd - tmin;
+        if (T->nL + T->nR > Nd) {
+            T->nL = Nd;
+            T->nR = 0;
+        }
+    }
+    T->QX = Nx > 32 ? 64 : 32;
+    T->QY = std::min(16, std::max(1, Ny));
+    const int nfold = T->nL + T->nR;
+    for (int it = 0; it < 8; ++it) {
+        int vx = 1, vy = 1, gwid = 1, gh = 1;
+        for (int q0 = 0; q0 < Nx; q0 += T->QX) {
+            const AxRange R = ax_range(T->aj[2], d->pad, q0, std::min(Nx, q0 + T->QX) - 1);
+            vx = std::max(vx, R.vhi - R.vlo + 1);
+            if (R.ahi >= R.alo) gwid = std::max(gwid, (R.ahi - R.alo) * T->aj[2].r + T->aj[2].span);
+        }
+        for (int q0 = 0; q0 < Ny; q0 += T->QY) {
+            const AxRange R = ax_range(T->aj[1], d->pad, q0, std::min(Ny, q0 + T->QY) - 1);
+            vy = std::max(vy, R.vhi - R.vlo + 1);
+            if (R.ahi >= R.alo) gh = std::max(gh, (R.ahi - R.alo) * T->aj[1].r + T->aj[1].span);
+        }
+        T->VXcap = vx;
+        T->VYcap = vy;
+        T->GBW = (gwid + T->align - 1 + T->align - 1) / T->align * T->align;
+        T->GBH = gh;
+        const size_t gbytes = (size_t)T->GBW * T->GBH * es;
+        const size_t obytes = (size_t)T->VYcap * T->QX * 4;
+        T->buf_bytes = (int)((std::max(gbytes, obytes) + 127) / 128 * 128);
+        T->stages = T->buf_bytes <= 8 * 1024 ? 4 : T->buf_bytes <= 16 * 1024 ? 3 : 2;
+        const size_t plane = (size_t)T->QY * T->QX * 4;
+        size_t off = (size_t)T->stages * T->buf_bytes;
+        T->fx_off = (int)off;
+        off += (size_t)T->GBH * T->VXcap * 4;
+        T->ring_off = (int)off;
+        off += (size_t)JD.span * plane;
+        T->facc_off = (int)off;
+        off += (size_t)nfold * plane;
+        T->w_off = (int)off;
+        off += (size_t)(T->aj[0].s + T->aj[1].s + T->aj[2].s) * w * 4;
+        T->tab_off = (int)off;
+        off += (size_t)(T->VXcap + T->VYcap) * 4;
+        T->bar_off = (int)((off + 15) / 16 * 16);
+        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 8 * T->stages <= 54 * 1024) break;
+        if (T->QY > 8) T->QY /= 2;
+        else if (T->QX > 32) T->QX /= 2;
+        else break;
+    }
+    if (T->GBW > 256 || T->GBH > 256 || T->bar_off + 8 * T->stages > 200 * 1024) return -1;
+    T->qtiles_x = (Nx + T->QX - 1) / T->QX;
+    T->qtiles_y = (Ny + T->QY - 1) / T->QY;
+    const long long base = (long long)T->qtiles_x * T->qtiles_y * d->n * d->c;
+    const long long want = 152LL * 4 * 4;
+    const long long chunks = std::max(1LL, std::min<long long>(Nd, (want + base - 1) / base));
+    T->QD = (int)((Nd + chunks - 1) / chunks);
+    T->qtiles_d = (Nd + T->QD - 1) / T->QD;
+    const long long ntiles = base * T->qtiles_d;
+    if (ntiles >= (1LL << 31)) return -1;
+    T->ntiles = (int)ntiles;
+    T->gy = gy;
+    T->gx = gx;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return -1;
+    const cuuint64_t Wg = (cuuint64_t)T->aj[2].n_g, Hg = (cuuint64_t)T->aj[1].n_g, Dg = (cuuint64_t)JD.n_g;
+    cuuint64_t dims[4] = {Wg, Hg, Dg, (cuuint64_t)(d->n * d->c)};
+    cuuint64_t strides[3] = {Wg * es, Wg * Hg * es, Wg * Hg * Dg * es};
+    cuuint32_t box[4] = {(cuuint32_t)T->GBW, (cuuint32_t)T->GBH, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (enc(&T->tmap, dt, 4, const_cast<void*>(gy), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return -1;
+    *ntk = w;
+    return FCFS_OK;
+}
+
 // Plan the bulk-copy weight-gradient kernel (1D/2D, x and gy in the same
 // storage type, 16-byte row pitches).  The grid is fixed by the tile's
 // shared-memory footprint on a 152-SM GB300, so the workspace size and the
@@ -922,6 +1038,16 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
         }
         clear_error();
     }
+    if (gx && is3d) {
+        TmaDx3Params T;
+        int ntd = 0;
+        if (plan_dx3_tma(d, B, gy, gx, &T, &ntd) == FCFS_OK) {
+            cudaError_t e = launch_dx3d_tma(T, ntd, d->dtype_out, st);
+            if (e != cudaSuccess) return cuda_fail(e, "3D input-gradient (bulk-copy) launch");
+            gx = nullptr;  // done
+        }
+        clear_error();
+    }
     if (gx) {
         plan_dx(B, is3d);
         if (is3d && B.GDcap > 256) return fail(FCFS_ERR_UNSUPPORTED, "depth ratio needs more than 256 gradient planes per tile");
@@ -977,13 +1103,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // The bulk-tensor path needs a 16-byte aligned base, rows whose byte pitch is
 // a multiple of 16, and extents a tensor map can describe.
 bool tma_eligible(const fcfs_desc* d, const void* x) {
-    if (d->ndim > 2) return false;
     const int es = dtype_size(d->dtype_in);
     const long long W = d->in_shape[d->ndim - 1];
-    const long long H = d->ndim == 2 ? d->in_shape[0] : 1;
+    const long long H = d->ndim >= 2 ? d->in_shape[d->ndim - 2] : 1;
+    const long long D = d->ndim == 3 ? d->in_shape[0] : 1;
     if (((uintptr_t)x) % 16) return false;
     if ((W * es) % 16) return false;
-    if (W >= (1LL << 31) || H >= (1LL << 31) || d->n * d->c >= (1LL << 31)) return false;
+    if (W >= (1LL << 31) || H >= (1LL << 31) || D >= (1LL << 31) || d->n * d->c >= (1LL << 31)) return false;
+    if (d->ndim == 3 && d->dtype_in != d->dtype_out) return false;
+    if (d->ndim == 3 && d->dtype_in == FCFS_U8) return false;
     long long oplane = 1;
     for (int a = 0; a < d->ndim; ++a) oplane *= d->out_shape[a];
     if (oplane >= (1LL << 31)) return false;  // 32-bit offsets within an output plane
@@ -1004,7 +1132,10 @@ static void tma_sizes(const FwdParams& P, int es, int* BW, int* BH, int* buf_byt
 // 256-thread CTAs; output columns ~128 (an even count), rows as the
 // shared-memory budget allows (3+ CTAs per SM, tiles of ~16-32 outputs per
 // thread so per-tile work amortizes).
-TileChoice default_tma_tiles(const FwdParams& P0, int es) {
+TileChoice default_tma3_tiles(const FwdParams& P0, int es);
+
+TileChoice default_tma_tiles(const FwdParams& P0, int es, bool is3d) {
+    if (is3d) return default_tma3_tiles(P0, es);
     FwdParams P = P0;
     const int rx = P.ax[2].r, ry = P.ax[1].r;
     int WX = std::max(1, 128 / rx);
@@ -1053,10 +1184,111 @@ int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T, int thr
     return FCFS_OK;
 }
 
+// 3D bulk-copy forward: staging box, plane buffers, the x-pass intermediate,
+// the ring of span_d y-interpolated planes and the weights, in that order.
+static void tma3_sizes(const FwdParams& P, int es, TmaFwd3Params* T) {
+    T->align = 16 / es;
+    T->BW = box_width(P.IC, T->align);
+    T->BH = P.IR;
+    T->buf_bytes = (T->BW * T->BH * es + 127) / 128 * 128;
+    // plane copies in flight: a plane is small next to the latency of one copy
+    T->stages = T->buf_bytes <= 12 * 1024 ? 4 : T->buf_bytes <= 24 * 1024 ? 3 : 2;
+    size_t off = (size_t)T->stages * T->buf_bytes;
+    T->sh_off = (int)off;
+    off += (size_t)P.IR * P.OX * 4;
+    T->ring_off = (int)off;
+    off += (size_t)P.ring * P.OY * P.OX * 4;
+    T->w_off = (int)off;
+    off += (size_t)(P.ax[0].r + P.ax[1].r + P.ax[2].r) * P.ax[2].nt * 4;
+    T->bar_off = (int)((off + 15) / 16 * 16);
+}
+
+size_t forward3_tma_smem_bytes(const TmaFwd3Params& T) { return (size_t)T.bar_off + 8 * T.stages; }
+
+// Tiles of ~128 output columns and 16-32 output rows (the ring of span_d
+// planes dominates shared memory; 3 CTAs per SM), depth chunks so that every
+// CTA of the persistent grid gets several tiles.
+TileChoice default_tma3_tiles(const FwdParams& P0, int es) {
+    FwdParams P = P0;
+    const int rx = P.ax[2].r, ry = P.ax[1].r;
+    int WX = std::max(1, 128 / rx);
+    while (WX > 1 && (WX * rx) % 4) --WX;  // 4-wide column groups in the register-blocked kernel
+    int WY = std::max(1, 24 / ry);
+    for (int it = 0; it < 64; ++it) {
+        apply_tiles(P, true, WX, WY, 1, 0);
+        TmaFwd3Params T;
+        tma3_sizes(P, es, &T);
+        if (T.BW <= 256 && T.BH <= 256 && forward3_tma_smem_bytes(T) <= 72 * 1024) break;
+        if (T.BW > 256 && WX > 1) WX = std::max(1, WX * 3 / 4);
+        else if (WY > 1) WY = std::max(1, WY * 3 / 4);
+        else if (WX > 1) WX = std::max(1, WX * 3 / 4);
+        else break;
+    }
+    // same number of tiles, spread evenly (no thin last tile)
+    {
+        const int nx = P.ax[2].n_win, ny = P.ax[1].n_win;
+        const int tx = (nx + WX - 1) / WX, ty = (ny + WY - 1) / WY;
+        int wx = (nx + tx - 1) / tx;
+        while ((wx * rx) % 4 && wx < WX) ++wx;
+        if ((wx * rx) % 4 == 0 || wx == WX) WX = wx;
+        WY = (ny + ty - 1) / ty;
+        apply_tiles(P, true, WX, WY, 1, 0);
+    }
+    const long long base = (long long)P.tiles_x * P.tiles_y * P.planes;
+    const long long want = 152LL * 3 * 6;
+    const long long chunks = std::max(1LL, (want + base - 1) / base);
+    const int WD = (int)std::max(1LL, (P.ax[0].n_win + chunks - 1) / chunks);
+    TileChoice t{WX, WY, std::max(WD, 2)};
+    t.G = 0;
+    t.tma = 1;
+    return t;
+}
+
+int prepare_tma3(const fcfs_desc* d, const FwdParams& P, TmaFwd3Params* T, int threads) {
+    memset(T, 0, sizeof(*T));
+    T->P = P;
+    const int es = dtype_size(d->dtype_in);
+    tma3_sizes(P, es, T);
+    if (T->BW > 256 || T->BH > 256) return fail(FCFS_ERR_UNSUPPORTED, "tile too large for one bulk copy");
+    T->threads = threads > 0 ? threads : 256;
+    if (P.OX > T->threads) return fail(FCFS_ERR_UNSUPPORTED, "tile wider than the CTA");
+    if (P.ax[2].nt > 5) return fail(FCFS_ERR_UNSUPPORTED, "3D bulk-copy path takes at most 5 taps per phase");
+    const long long nt = (long long)P.tiles_x * P.tiles_y * P.tiles_d * P.planes;
+    if (nt >= (1LL << 31)) return fail(FCFS_ERR_UNSUPPORTED, "too many tiles");
+    T->ntiles = (int)nt;
+    const cuuint64_t W = (cuuint64_t)P.ax[2].n_in, H = (cuuint64_t)P.ax[1].n_in, D = (cuuint64_t)P.ax[0].n_in;
+    cuuint64_t dims[4] = {W, H, D, (cuuint64_t)P.planes};
+    cuuint64_t strides[3] = {W * es, W * H * es, W * H * D * es};
+    cuuint32_t box[4] = {(cuuint32_t)T->BW, (cuuint32_t)T->BH, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt =
+        d->dtype_in == FCFS_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = encode_fn()(&T->tmap, dt, 4, const_cast<void*>(P.x), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(FCFS_ERR_UNSUPPORTED, "tensor map encode failed (%d)", (int)r);
+    return FCFS_OK;
+}
+
 // Launch the forward with a tile choice: the TMA-staged persistent kernel
 // when the choice asks for it and the layout allows, else the gather kernel.
 int launch_choice(const fcfs_desc* d, FwdParams& P, int ntk, const TileChoice& t, cudaStream_t st) {
     const bool is3d = d->ndim == 3;
+    if (t.tma == 1 && is3d && tma_eligible(d, P.x)) {
+        apply_tiles(P, true, t.WX, t.WY, t.WD, 0);
+        TmaFwd3Params T;
+        int rc = prepare_tma3(d, P, &T, t.threads);
+        if (rc == FCFS_OK && forward3_tma_smem_bytes(T) <= 200 * 1024) {
+            if (t.rs != 0) {
+                cudaError_t e = launch_forward3d_rs(T, d->dtype_in, d->dtype_out, st);
+                if (e == cudaSuccess) return FCFS_OK;
+                if (e != cudaErrorInvalidValue) return cuda_fail(e, "3D forward (register-blocked) launch");
+            }
+            cudaError_t e = launch_forward3d_tma(T, ntk, d->dtype_in, d->dtype_out, st);
+            return e == cudaSuccess ? FCFS_OK : cuda_fail(e, "3D forward (bulk-copy) launch");
+        }
+        clear_error();
+    }
     if (t.tma == 1 && !is3d && tma_eligible(d, P.x)) {
         apply_tiles(P, false, t.WX, t.WY, 1, t.G);
         TmaFwdParams T;

@@ -39,7 +39,9 @@ int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* 
 void apply_tiles(FwdParams& P, bool is3d, int WX, int WY, int WD, int G = 0);
 bool tma_eligible(const fcfs_desc* d, const void* x);
 int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T, int threads = 256);
-TileChoice default_tma_tiles(const FwdParams& P, int es);
+TileChoice default_tma_tiles(const FwdParams& P, int es, bool is3d = false);
+int prepare_tma3(const fcfs_desc* d, const FwdParams& P, TmaFwd3Params* T, int threads = 256);
+size_t forward3_tma_smem_bytes(const TmaFwd3Params& T);
 int launch_choice(const fcfs_desc* d, FwdParams& P, int ntk, const TileChoice& t, cudaStream_t st);
 TileChoice default_tiles(const FwdParams& P, bool is3d);
 void set_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice t);

@@ -144,6 +144,29 @@ struct TmaDxParams {
     int rs_span, WAcap, FXP;
 };
 
+// Bulk-copy staged input-gradient parameters (3D): the 2D tile of real
+// (y, x) indices plus a chunk of QD real depth indices; g planes stream
+// through a ring of aj[0].span adjoint-interpolated planes.  Depth indices
+// that receive folded padding contributions, [0, nL) and [D - nR, D), are
+// accumulated in shared memory and stored at the end of their chunk.
+struct TmaDx3Params {
+    CUtensorMap tmap;   // gy viewed as [planes][Do][Ho][Wo]
+    AxisP ax[3];
+    AdjP aj[3];
+    int C, pad;
+    int QX, QY, QD;
+    int qtiles_x, qtiles_y, qtiles_d;
+    int GBW, GBH, align;
+    int VXcap, VYcap;
+    int nL, nR;
+    int stages;  // g plane buffers in flight (2..4)
+    int buf_bytes, fx_off, ring_off, facc_off, w_off, tab_off, bar_off;
+    int threads;
+    int ntiles;
+    const void* gy;
+    void* gx;
+};
+
 // Bulk-copy staged weight-gradient parameters (1D/2D): forward tile
 // geometry, tensor maps of x and gy, and the record layout of the partials.
 struct TmaDwParams {
@@ -159,6 +182,18 @@ struct TmaDwParams {
     float* ws;               // [grid][maxseg][rec] floats, then [grid][maxseg] plane ids
     float* gw[3];
     long long n;
+};
+
+// Bulk-copy staged 3D forward: FwdParams (with depth tiling), the tensor map
+// of the input viewed as [planes][D][H][W], staging box and shared layout.
+struct TmaFwd3Params {
+    CUtensorMap tmap;
+    FwdParams P;
+    int BW, BH, align;
+    int stages;  // plane buffers in flight (2..4)
+    int buf_bytes, sh_off, ring_off, w_off, bar_off;
+    int threads;
+    int ntiles;
 };
 
 struct NearestParams {
@@ -266,6 +301,9 @@ int read_status_fwd_tma(int clear);
 int read_status_bwd_tma(int clear);
 cudaError_t launch_dx_tma(const TmaDxParams& T, int nt, int dg, int dx, cudaStream_t st);
 cudaError_t launch_dx_rs(const TmaDxParams& T, int dt, cudaStream_t st);
+cudaError_t launch_forward3d_tma(const TmaFwd3Params& T, int nt, int din, int dout, cudaStream_t st);
+cudaError_t launch_forward3d_rs(const TmaFwd3Params& T, int din, int dout, cudaStream_t st);
+cudaError_t launch_dx3d_tma(const TmaDx3Params& T, int nt, int dt, cudaStream_t st);
 bool dx_rs_compiled(int S, int span);
 cudaError_t launch_dw_tma(const TmaDwParams& T, int nt, int dt, cudaStream_t st, const void* x);
 size_t forward_smem_bytes(const FwdParams& P, bool is3d);

@@ -33,43 +33,54 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     const bool is3d = d->ndim == 3;
     const bool tma = tma_eligible(d, x);
     std::vector<TileChoice> cands;
-    TileChoice def = tma ? default_tma_tiles(P0, dtype_size(d->dtype_in)) : default_tiles(P0, is3d);
+    TileChoice def = tma ? default_tma_tiles(P0, dtype_size(d->dtype_in), is3d) : default_tiles(P0, is3d);
     def.tma = tma ? 1 : 0;
     cands.push_back(def);
     const int ox_targets[] = {64, 128, 192, 256};
     const int oy_targets[] = {8, 16, 32, 48, 64};
     const int ry = P0.ax[1].r;
+    // 3D: depth windows per tile as well (half, same, double the default)
+    const int wd_scale[] = {2, 4, 8};
     for (int oxt : ox_targets)
         for (int oyt : oy_targets)
-            for (int gm = 0; gm < 4; ++gm) {
-                TileChoice t{std::max(1, oxt / P0.ax[2].r), std::max(1, oyt / ry), def.WD};
-                t.tma = def.tma;
-                // TMA kernel: the second variant is the 512-thread CTA; gather kernel: thread groups
-                t.G = tma ? 0 : (gm == 0 ? def.G : (def.G == ry ? 1 : ry));
-                t.threads = tma ? ((gm & 1) == 0 ? 256 : 512) : 0;
-                t.rs = gm < 2 ? 1 : 0;
-                if (!tma && gm >= 2) continue;
-                FwdParams P = P0;
-                apply_tiles(P, is3d, t.WX, t.WY, t.WD, t.G);
-                if (!tma && P.OX * P.G > 512) continue;
-                if (tma) {
-                    TmaFwdParams T;
-                    if (prepare_tma(d, P, &T, t.threads) != FCFS_OK || forward_tma_smem_bytes(T) > 200 * 1024) {
-                        clear_error();
+            for (int gm = 0; gm < 4; ++gm)
+                for (int ws : wd_scale) {
+                    if (!is3d && ws != 4) continue;
+                    TileChoice t{std::max(1, oxt / P0.ax[2].r), std::max(1, oyt / ry), std::max(1, def.WD * ws / 4)};
+                    t.tma = def.tma;
+                    // TMA kernel: the second variant is the 512-thread CTA; gather kernel: thread groups
+                    t.G = tma ? 0 : (gm == 0 ? def.G : (def.G == ry ? 1 : ry));
+                    t.threads = tma ? ((gm & 1) == 0 ? 256 : 512) : 0;
+                    t.rs = gm < 2 ? 1 : 0;
+                    if (!tma && gm >= 2) continue;
+                    FwdParams P = P0;
+                    apply_tiles(P, is3d, t.WX, t.WY, t.WD, t.G);
+                    if (!tma && P.OX * P.G > 512) continue;
+                    if (tma && is3d) {
+                        TmaFwd3Params T;
+                        if (prepare_tma3(d, P, &T, t.threads) != FCFS_OK || forward3_tma_smem_bytes(T) > 200 * 1024) {
+                            clear_error();
+                            continue;
+                        }
+                    } else if (tma) {
+                        TmaFwdParams T;
+                        if (prepare_tma(d, P, &T, t.threads) != FCFS_OK || forward_tma_smem_bytes(T) > 200 * 1024) {
+                            clear_error();
+                            continue;
+                        }
+                    } else if (forward_smem_bytes(P, is3d) > 200 * 1024) {
                         continue;
                     }
-                } else if (forward_smem_bytes(P, is3d) > 200 * 1024) {
-                    continue;
+                    t.WX = P.WX;
+                    t.WY = P.WY;
+                    t.WD = P.WD;
+                    t.G = tma ? 0 : P.G;
+                    bool dup = false;
+                    for (auto& c : cands)
+                        dup |= (c.WX == t.WX && c.WY == t.WY && c.WD == t.WD && c.G == t.G && c.tma == t.tma &&
+                                c.threads == t.threads && c.rs == t.rs);
+                    if (!dup) cands.push_back(t);
                 }
-                t.WX = P.WX;
-                t.WY = P.WY;
-                t.G = tma ? 0 : P.G;
-                bool dup = false;
-                for (auto& c : cands)
-                    dup |= (c.WX == t.WX && c.WY == t.WY && c.G == t.G && c.tma == t.tma && c.threads == t.threads &&
-                            c.rs == t.rs);
-                if (!dup) cands.push_back(t);
-            }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(FCFS_ERR_CUDA, "event create failed");

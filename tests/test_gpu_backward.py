@@ -86,9 +86,35 @@ def test_dx_1d_and_tiny(F, orc, ratio, pad):
 
 @pytest.mark.parametrize("ratios", [((3, 2),) * 3, ((2, 3), (4, 3), (5, 4))])
 @pytest.mark.parametrize("pad", (REPL, CONST, REFL))
-def test_dx_3d(F, orc, ratios, pad):
-    for method in (BILINEAR, BICUBIC):
-        check_dx(F, orc, (1, 2, 17, 21, 37), [F.Axis(r, s, method) for r, s in ratios], pad)
+@pytest.mark.parametrize("width", (37, 48))
+def test_dx_3d(F, orc, ratios, pad, width):
+    # width 48 gives g rows of 16-byte multiples (the bulk-copy volume kernel), 37 the gather kernel
+    for method in (NEAREST, BILINEAR, BICUBIC):
+        check_dx(F, orc, (1, 2, 17, 21, width), [F.Axis(r, s, method) for r, s in ratios], pad)
+
+
+@pytest.mark.parametrize("ratios", [((3, 2),) * 3, ((2, 3), (4, 3), (5, 4)), ((1, 2), (3, 1), (2, 1))])
+@pytest.mark.parametrize("pad", (REPL, REFL))
+def test_dx_3d_bf16(F, orc, ratios, pad):
+    check_dx(F, orc, (2, 2, 13, 18, 64), [F.Axis(r, s, BICUBIC) for r, s in ratios], pad, dtype=torch.bfloat16,
+             seed=5)
+
+
+@pytest.mark.parametrize("pad", (REPL, CONST, REFL))
+def test_dx_3d_tiny_and_many_tiles(F, orc, pad):
+    for shape in ((1, 1, 1, 3, 8), (1, 1, 2, 1, 16), (1, 1, 3, 5, 8), (1, 1, 5, 2, 24)):
+        for method in (BILINEAR, BICUBIC):
+            check_dx(F, orc, shape, [F.Axis(3, 2, method)] * 3, pad)
+    # depth chunks, ragged tiles on every axis, several tiles per CTA
+    check_dx(F, orc, (3, 2, 41, 37, 136), [F.Axis(5, 4, BICUBIC), F.Axis(2, 3, BILINEAR), F.Axis(3, 2, BICUBIC)],
+             pad, seed=9)
+
+
+def test_dx_3d_learnable(F, orc):
+    g = torch.Generator().manual_seed(12)
+    axes = [F.Axis(r, s, BILINEAR, 2, (torch.randn((2, r, 5), generator=g) * 0.5).cuda())
+            for r, s in ((3, 2), (5, 4), (3, 2))]
+    check_dx(F, orc, (1, 2, 11, 13, 48), axes, REPL, seed=13)
 
 
 def _learn_axes(F, C, ratios, K, per_channel, seed):

@@ -143,9 +143,36 @@ def test_1d(F, orc, ratio, method, length):
 @pytest.mark.parametrize("ratios", [((3, 2),) * 3, ((2, 3), (4, 3), (5, 4)), ((1, 2), (3, 1), (2, 11))])
 @pytest.mark.parametrize("method", (NEAREST, BILINEAR, BICUBIC))
 @pytest.mark.parametrize("pad", (REPL, CONST, REFL))
-def test_3d(F, orc, ratios, method, pad):
-    x = inputs.uniform((1, 2, 19, 23, 41), 41)
+@pytest.mark.parametrize("width", (41, 44))
+def test_3d(F, orc, ratios, method, pad, width):
+    # width 44 (16-byte rows) takes the bulk-copy volume kernel, 41 the gather kernel
+    x = inputs.uniform((1, 2, 19, 23, width), 41)
     check_forward(F, orc, x, [F.Axis(r, s, method) for r, s in ratios], pad, pad_value=-0.5)
+
+
+@pytest.mark.parametrize("ratios", [((3, 2),) * 3, ((2, 3), (4, 3), (5, 4))])
+@pytest.mark.parametrize("method", (BILINEAR, BICUBIC))
+@pytest.mark.parametrize("pad", (REPL, REFL))
+def test_3d_bf16_storage(F, orc, ratios, method, pad):
+    x = inputs.normal((2, 2, 17, 30, 48), 42, dtype=torch.bfloat16)
+    check_forward(F, orc, x, [F.Axis(r, s, method) for r, s in ratios], pad)
+
+
+@pytest.mark.parametrize("ratio,method", [((3, 2), BILINEAR), ((2, 1), BILINEAR), ((4, 3), BILINEAR),
+                                          ((2, 3), BILINEAR), ((3, 2), BICUBIC)])
+@pytest.mark.parametrize("width", (48, 44))
+@pytest.mark.parametrize("dtype", (torch.float32, torch.bfloat16))
+def test_3d_register_blocked(F, orc, ratio, method, width, dtype):
+    # one phase count and span on all axes: the register-blocked volume kernel (4- or 2-wide columns)
+    x = inputs.uniform((2, 2, 19, 23, width), 44, dtype=dtype)
+    for pad in (REPL, CONST, REFL):
+        check_forward(F, orc, x, [F.Axis(*ratio, method)] * 3, pad, pad_value=0.25)
+
+
+def test_3d_many_tiles(F, orc):
+    # several tiles per CTA of the persistent grid, depth chunks, ragged last tiles
+    x = inputs.uniform((3, 2, 37, 70, 132), 43)
+    check_forward(F, orc, x, [F.Axis(3, 2, BILINEAR), F.Axis(4, 3, BICUBIC), F.Axis(5, 4, BILINEAR)], REPL)
 
 
 @pytest.mark.parametrize("per_channel", (True, False))
@@ -163,10 +190,11 @@ def test_learnable_weights(F, orc, per_channel, ratios, K, pad):
         check_forward(F, orc, x, axes, pad, pad_value=0.25)
 
 
-def test_learnable_3d(F, orc):
+@pytest.mark.parametrize("width", (29, 28))
+def test_learnable_3d(F, orc, width):
     g = torch.Generator().manual_seed(3)
     axes = [F.Axis(r, s, BILINEAR, 2, torch.randn((2, r, 5), generator=g).cuda()) for r, s in ((3, 2), (5, 4), (2, 3))]
-    x = inputs.normal((1, 2, 11, 13, 29), 52)
+    x = inputs.normal((1, 2, 11, 13, width), 52)
     check_forward(F, orc, x, axes, REPL)
 
 
@@ -211,6 +239,19 @@ def test_tuned_plan_same_result(F):
     after = F.resize(x, axes)
     F.fcfs_clear_plans()
     # tile shape changes the work split, never the arithmetic order of one output
+    assert torch.equal(before, after)
+
+
+def test_tuned_plan_same_result_3d(F):
+    x = inputs.uniform((1, 2, 40, 48, 64), 92).cuda()
+    axes = [F.Axis(3, 2, BILINEAR)] * 3
+    before = F.resize(x, axes)
+    d = F.make_desc(x.shape, axes, 0, 0)
+    y = torch.empty_like(before)
+    ms, n = F.fcfs_tune_forward(d, x.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream, 2)
+    assert n >= 2 and ms > 0
+    after = F.resize(x, axes)
+    F.fcfs_clear_plans()
     assert torch.equal(before, after)
 
 
