@@ -73,6 +73,7 @@ __device__ __forceinline__ void issue3(const TmaDx3Params& T, const Dx3Geo& g, i
 struct CursorDx3 {
     Dx3Geo g;
     int tile, gd, n;
+    int k;  // stage of the next job to issue
 };
 
 template <typename Tg>
@@ -86,9 +87,9 @@ __device__ __forceinline__ void issue_next(const TmaDx3Params& T, CursorDx3& c, 
         } while (c.g.g_last < c.g.g_first);
         c.gd = c.g.g_first;
     }
-    const int k = c.n % T.stages;
-    issue3<Tg>(T, c.g, c.gd, smem + k * T.buf_bytes, &bars[k]);
+    issue3<Tg>(T, c.g, c.gd, smem + c.k * T.buf_bytes, &bars[c.k]);
     ++c.n;
+    if (++c.k == T.stages) c.k = 0;
 }
 
 template <int NT>
@@ -116,7 +117,7 @@ __device__ __forceinline__ int depth_target(const TmaDx3Params& T, int v) {
 }
 
 template <int NT, typename Tg, typename Tx>
-__global__ void __launch_bounds__(256, 4) fcfs_bwd_dx3d_tma(const __grid_constant__ TmaDx3Params T) {
+__global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constant__ TmaDx3Params T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ CursorDx3 cur;
     const AdjP &JD = T.aj[0], &JY = T.aj[1], &JX = T.aj[2];
@@ -149,11 +150,14 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx3d_tma(const __grid_constan
         while (cur.g.g_last < cur.g.g_first && ++cur.tile < t_end) cur.g = dx3_geo(T, cur.tile);
         cur.gd = cur.g.g_first;
         cur.n = 0;
+        cur.k = 0;
         for (int k = 0; k < S; ++k) issue_next<Tg>(T, cur, t_end, smem_raw, bars);
     }
     __syncthreads();
     const bool learn = T.ax[0].learn || T.ax[1].learn || T.ax[2].learn;
-    int cur_c = -1, job = 0;
+    int cur_c = -1;
+    int stg = 0;         // stage of the current job
+    uint32_t phase = 0;  // its barrier phase
     for (int tile = t_begin; tile < t_end; ++tile) {
         const Dx3Geo gt = dx3_geo(T, tile);
         Tx* xpl = static_cast<Tx*>(T.gx) + (long long)gt.plane * Nd * Ny * Nx;
@@ -191,14 +195,14 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx3d_tma(const __grid_constan
             ytab[vr] = u << 16 | ((a - gt.Y.alo) * JY.r + JY.off[u]);
         }
         int ad = gt.Dr.alo;  // next adjoint depth window to form
-        for (int gd = gt.g_first; gd <= gt.g_last; ++gd, ++job) {
-            const int stg = job % S;
+        int rslot = 0;  // ring slot of g plane gd
+        for (int gd = gt.g_first; gd <= gt.g_last; ++gd) {
             unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
             // one warp waits for the copy; the barrier releases the others
-            if (threadIdx.x < 32) mbar_wait(&bars[stg], (uint32_t)((job / S) & 1), &g_status_bwd_tma);
+            if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
             __syncthreads();
             const Tg* G0 = reinterpret_cast<const Tg*>(bufk);
-            float* slot = ring + ((gd - gt.g_first) % ringn) * plane_sz;
+            float* slot = ring + rslot * plane_sz;
             if (gd < 0 || gd >= JD.n_g) {
                 // outside the forward output: a zero plane
                 if (col_ok)
@@ -281,7 +285,6 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx3d_tma(const __grid_constan
             // ---- depth: every adjoint window whose g planes are all in the ring
             // (a thread reads and writes only its own (y, x) positions)
             while (ad <= gt.Dr.ahi && ad * JD.r + JD.lo_in + JD.span <= gd + 1) {
-                const int pb = ad * JD.r + JD.lo_in - gt.g_first;
                 for (int u = 0; u < JD.s; ++u) {
                     const int v = ad * JD.s + JD.lo_out + u;
                     if (v < gt.Dr.vlo || v > gt.Dr.vhi) continue;
@@ -289,13 +292,17 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx3d_tma(const __grid_constan
                     if (tq < gt.qd0 || tq >= gt.qd0 + gt.nqd) continue;
                     const int fs = fold_slot(T, tq);
                     if (!col_ok) continue;
+                    // the window completes at plane gd: its plane k sits in slot (rslot + 1 + k) mod span
                     float w[NT];
                     const float* rp[NT];
-                    const int p0 = pb + JD.off[u];
+                    const int sb = rslot + 1 + JD.off[u];
 #pragma unroll
                     for (int t = 0; t < NT; ++t) {
                         w[t] = sWd[u * NT + t];
-                        rp[t] = ring + ((p0 + t) % ringn) * plane_sz + cl;
+                        int sl = sb + t;
+                        if (sl >= ringn) sl -= ringn;
+                        if (sl >= ringn) sl -= ringn;
+                        rp[t] = ring + sl * plane_sz + cl;
                     }
                     for (int qyl = gq; qyl < gt.nqy; qyl += G) {
                         float acc = 0.f;
@@ -309,6 +316,11 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx3d_tma(const __grid_constan
             }
             __syncthreads();  // the ring slot, sF and this stage are free again
             if (threadIdx.x == 0) issue_next<Tg>(T, cur, t_end, smem_raw, bars);
+            if (++rslot == ringn) rslot = 0;
+            if (++stg == S) {
+                stg = 0;
+                phase ^= 1;
+            }
         }
         // ---- chunk end: folded indices, and real indices no adjoint window reaches
         if (col_ok) {

@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ 
     __shared__ float sWFx[S * SPAN], sWFy[S * SPAN];
     const AdjP& JX = T.aj[2];
     const AdjP& JY = T.aj[1];
-    unsigned char* bufs[2] = {smem_raw, smem_raw + T.buf_bytes};
+    unsigned char* const buf0 = smem_raw;
+    unsigned char* const buf1 = smem_raw + T.buf_bytes;
     float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
     const int QX = T.QX, GBW = T.GBW, FXP = T.FXP, R = JX.r;
@@ -58,14 +59,14 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ 
     int tile = blockIdx.x * per;
     const int tile_end = min(ntiles, tile + per);
     if (tile >= tile_end) return;
-    if (threadIdx.x == 0) issue<Tg>(T, dx_geo(T, tile), bufs[0], &bars[0]);
+    if (threadIdx.x == 0) issue<Tg>(T, dx_geo(T, tile), buf0, &bars[0]);
     const bool learn = T.ax[2].learn || T.ax[1].learn;
     int cur_c = -1;
     for (int k = 0; tile < tile_end; ++k, ++tile) {
         const DxGeo geo = dx_geo(T, tile);
-        const Tg* G0 = reinterpret_cast<const Tg*>(bufs[k & 1]);
+        const Tg* G0 = reinterpret_cast<const Tg*>((k & 1) ? buf1 : buf0);
         if (threadIdx.x == 0 && tile + 1 < tile_end)
-            issue<Tg>(T, dx_geo(T, tile + 1), bufs[(k + 1) & 1], &bars[(k + 1) & 1]);
+            issue<Tg>(T, dx_geo(T, tile + 1), (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
         mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
             stage_adj_span<S, SPAN>(sWFx, T.ax[2], JX, geo.c);
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ 
         }
         // ---- pass y (adjoint along y) on the tile's real columns
         const bool ypath_smem = geo.Y.left || geo.Y.right || !geo.Y.covered;
-        float* sO = reinterpret_cast<float*>(bufs[k & 1]);  // the g tile is consumed
+        float* sO = reinterpret_cast<float*>((k & 1) ? buf1 : buf0);  // the g tile is consumed
         const int q = geo.qx0 + cl;
         const bool col_ok = g2 < G2 && cl < geo.nqx;
         const bool col_has = col_ok && q <= geo.X.vhi;

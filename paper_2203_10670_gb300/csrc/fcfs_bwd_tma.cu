@@ -38,57 +38,77 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const AdjP& JX = T.aj[2];
     const AdjP& JY = T.aj[1];
-    unsigned char* bufs[2] = {smem_raw, smem_raw + T.buf_bytes};
     float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
     float* sWx = reinterpret_cast<float*>(smem_raw + T.w_off);
     float* sWy = sWx + JX.s * NT;
+    int* xtab = reinterpret_cast<int*>(smem_raw + T.tab_off);  // per virtual column: u << 16 | g offset
+    int* ytab = xtab + T.VXcap;                                  // per virtual row: u << 16 | Fx row
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
+    const int S = T.stages;
     const int QX = T.QX, GBW = T.GBW, VXcap = T.VXcap;
     const int G = blockDim.x / QX;
     const int cl = threadIdx.x % QX, gq = threadIdx.x / QX;
     const bool active = gq < G;
     const int Nx = JX.n_x, Ny = JY.n_x;
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
     // each CTA owns a contiguous run of tiles (same plane for many tiles in a row)
     const int ntiles = (int)T.ntiles;
     const int per = (ntiles + gridDim.x - 1) / gridDim.x;
     int tile = blockIdx.x * per;
     const int tile_end = min(ntiles, tile + per);
     if (tile >= tile_end) return;
-    if (threadIdx.x == 0) issue<Tg>(T, dx_geo(T, tile), bufs[0], &bars[0]);
+    // geometry of the tile in each stage, computed once by the thread that issues its copy
+    __shared__ DxGeo sgeo[4];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+        for (int k = 0; k < S && tile + k < tile_end; ++k) {
+            sgeo[k] = dx_geo(T, tile + k);
+            issue<Tg>(T, sgeo[k], smem_raw + k * T.buf_bytes, &bars[k]);
+        }
+    }
+    __syncthreads();
     const bool learn = T.ax[2].learn || T.ax[1].learn;
     int cur_c = -1;
-    for (int k = 0; tile < tile_end; ++k, ++tile) {
-        const DxGeo geo = dx_geo(T, tile);
-        const Tg* G0 = reinterpret_cast<const Tg*>(bufs[k & 1]);
-        const int next = tile + 1;
-        if (threadIdx.x == 0 && next < tile_end) issue<Tg>(T, dx_geo(T, next), bufs[(k + 1) & 1], &bars[(k + 1) & 1]);
+    int stg = 0;
+    uint32_t phase = 0;
+    for (; tile < tile_end; ++tile) {
+        unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
+        // one warp waits for the copy; the barrier releases the others
+        if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
+        __syncthreads();
+        const DxGeo geo = sgeo[stg];
+        const int VX = geo.X.vhi - geo.X.vlo + 1;
+        const int VY = geo.Y.vhi - geo.Y.vlo + 1;
+        // the previous tile ended with a barrier: no thread still reads the weights or tables
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
             stage_adj_weights<NT>(sWx, T.ax[2], JX, geo.c);
             stage_adj_weights<NT>(sWy, T.ax[1], JY, geo.c);
             cur_c = geo.c;
         }
-        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        for (int cx = threadIdx.x; cx < VX; cx += blockDim.x) {
+            const int d = geo.X.vlo + cx - JX.lo_out;  // d >= 0: vlo >= vmin = lo_out
+            const int a = d / JX.s, u = d - a * JX.s;
+            xtab[cx] = u << 16 | ((a - geo.X.alo) * JX.r + JX.off[u]);
+        }
+        for (int vr = threadIdx.x; vr < VY; vr += blockDim.x) {
+            const int d = geo.Y.vlo + vr - JY.lo_out;
+            const int a = d / JY.s, u = d - a * JY.s;
+            ytab[vr] = u << 16 | ((a - geo.Y.alo) * JY.r + JY.off[u]);
+        }
         __syncthreads();
+        const Tg* G0 = reinterpret_cast<const Tg*>(bufk);
 
-        const int VX = geo.X.vhi - geo.X.vlo + 1;
         const int nGR = geo.Y.ahi >= geo.Y.alo ? (geo.Y.ahi - geo.Y.alo) * JY.r + JY.span : 0;
         // ---- pass x: adjoint along x for every staged g row, extended columns [vlo, vhi]
         if (active) {
             for (int cx = cl; cx < VX; cx += QX) {
-                const int d = geo.X.vlo + cx - JX.lo_out;
-                const int a = d / JX.s, u = d - a * JX.s;  // d >= 0: vlo >= vmin = lo_out
+                const int e = xtab[cx], u = e >> 16;
                 float w[NT];
 #pragma unroll
                 for (int t = 0; t < NT; ++t) w[t] = sWx[u * NT + t];
                 // taps past the phase's own count carry zero weights and stay inside the box
-                const Tg* src = G0 + gq * GBW + geo.xoff + (a - geo.X.alo) * JX.r + JX.off[u];
+                const Tg* src = G0 + gq * GBW + geo.xoff + (e & 0xffff);
                 float* dst = sF + gq * VXcap + cx;
 #pragma unroll 2
                 for (int gr = gq; gr < nGR; gr += G) {
@@ -120,32 +140,26 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
             }
             __syncthreads();
         }
-        // ---- pass y: adjoint along y on the real columns of the tile
+        // ---- pass y: adjoint along y on the real columns of the tile, one virtual row per step
         const bool ypath_smem = geo.Y.left || geo.Y.right || !geo.Y.covered;
-        float* sO = reinterpret_cast<float*>(bufs[k & 1]);  // the g tile is consumed
+        float* sO = reinterpret_cast<float*>(bufk);  // the g tile is consumed
         const int q = geo.qx0 + cl;
         const int fcol = q - geo.X.vlo;
         const bool col_ok = active && cl < geo.nqx;
         const bool col_has = col_ok && q <= geo.X.vhi;
         Tx* xcol = static_cast<Tx*>(T.gx) + (long long)geo.plane * Ny * Nx + q;
         if (col_ok) {
-            for (int u = gq; u < JY.s; u += G) {
-                float w[NT];
+            for (int vr = gq; vr < VY; vr += G) {
+                const int e = ytab[vr];
+                const float* src = sF + (e & 0xffff) * VXcap + fcol;
+                const float* w = sWy + (e >> 16) * NT;
+                float acc = 0.f;
+                if (col_has) {
 #pragma unroll
-                for (int t = 0; t < NT; ++t) w[t] = sWy[u * NT + t];
-                const float* src = sF + JY.off[u] * VXcap + fcol;
-                for (int a = geo.Y.alo; a <= geo.Y.ahi; ++a, src += JY.r * VXcap) {
-                    const int v = a * JY.s + JY.lo_out + u;
-                    if (v < geo.Y.vlo) continue;
-                    if (v > geo.Y.vhi) break;
-                    float acc = 0.f;
-                    if (col_has) {
-#pragma unroll
-                        for (int t = 0; t < NT; ++t) acc = fmaf(w[t], src[t * VXcap], acc);
-                    }
-                    if (ypath_smem) sO[(v - geo.Y.vlo) * QX + cl] = acc;
-                    else store_out(xcol + (long long)v * Nx, acc);
+                    for (int t = 0; t < NT; ++t) acc = fmaf(w[t], src[t * VXcap], acc);
                 }
+                if (ypath_smem) sO[vr * QX + cl] = acc;
+                else store_out(xcol + (long long)(geo.Y.vlo + vr) * Nx, acc);
             }
         }
         if (ypath_smem) {
@@ -164,13 +178,21 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();  // sF, the tables and this stage are free again
+        if (threadIdx.x == 0 && tile + S < tile_end) {
+            sgeo[stg] = dx_geo(T, tile + S);
+            issue<Tg>(T, sgeo[stg], bufk, &bars[stg]);
+        }
+        if (++stg == S) {
+            stg = 0;
+            phase ^= 1;
+        }
     }
 }
 
 template <int NT, typename Tg, typename Tx>
 cudaError_t run(const TmaDxParams& T, cudaStream_t st) {
-    const size_t smem = (size_t)T.bar_off + 16;
+    const size_t smem = (size_t)T.bar_off + 8 * T.stages;
     auto k = fcfs_bwd_dx2d_tma<NT, Tg, Tx>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -327,9 +349,9 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
     const FwdParams& P = T.P;
     const AxisP& AY = P.ax[1];
     const AxisP& AX = P.ax[2];
-    Tv* xb[2] = {reinterpret_cast<Tv*>(smem_raw), reinterpret_cast<Tv*>(smem_raw + T.xbuf_bytes)};
-    Tv* gb[2] = {reinterpret_cast<Tv*>(smem_raw + 2 * T.xbuf_bytes),
-                 reinterpret_cast<Tv*>(smem_raw + 2 * T.xbuf_bytes + T.gbuf_bytes)};
+    // stage b of the x and g copies (selected arithmetically: no local-memory pointer tables)
+    auto xb = [&](int b) { return reinterpret_cast<Tv*>(smem_raw + b * T.xbuf_bytes); };
+    auto gb = [&](int b) { return reinterpret_cast<Tv*>(smem_raw + 2 * T.xbuf_bytes + b * T.gbuf_bytes); };
     float* sH = reinterpret_cast<float*>(smem_raw + T.sh_off);
     float* sV = reinterpret_cast<float*>(smem_raw + T.sv_off);
     float* sWx = reinterpret_cast<float*>(smem_raw + T.w_off);
@@ -370,8 +392,8 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
         const DwGeo g = dw_geo(T, t);
         fence_proxy_async_smem();
         mbar_expect_tx(&bars[b], tx_bytes);
-        tma_load_3d(xb[b], &T.tmap_x, g.x_al, g.row0, g.plane, &bars[b]);
-        tma_load_3d(gb[b], &T.tmap_g, g.g_al, g.iy0 * AY.r, g.plane, &bars[b]);
+        tma_load_3d(xb(b), &T.tmap_x, g.x_al, g.row0, g.plane, &bars[b]);
+        tma_load_3d(gb(b), &T.tmap_g, g.g_al, g.iy0 * AY.r, g.plane, &bars[b]);
     };
     // write this CTA's accumulated partials as record `seg` for channel c
     auto flush = [&](int seg, int c) {
@@ -423,8 +445,8 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
     if (tile < tile_end && threadIdx.x == 0) issue(tile, 0);
     for (int k = 0; tile < tile_end; ++k, ++tile) {
         const DwGeo geo = dw_geo(T, tile);
-        Tv* X = xb[k & 1];
-        const Tv* Gt = gb[k & 1];
+        Tv* X = xb(k & 1);
+        const Tv* Gt = gb(k & 1);
         if (threadIdx.x == 0 && tile + 1 < tile_end) issue(tile + 1, (k + 1) & 1);
         const int ch = per_channel ? geo.c : 0;
         if (ch != cur_c) {

@@ -66,11 +66,14 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
         cur.g = geo3(T, t_begin);
         cur.p = cur.g.p_first;
         cur.n = 0;
+        cur.k = 0;
         for (int k = 0; k < S; ++k) issue_next<Tin>(T, cur, t_end, smem_raw, bars);
     }
     __syncthreads();
     const bool learn = AX.learn || AY.learn || AD.learn;
-    int cur_c = -1, job = 0;
+    int cur_c = -1;
+    int k = 0;           // stage of the current job
+    uint32_t phase = 0;  // its barrier phase
     for (int tile = t_begin; tile < t_end; ++tile) {
         const Geo3 geo = geo3(T, tile);
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
@@ -85,11 +88,11 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
         const bool col2 = act2 && oxy / R < geo.nwx && nvalid > 0;
         const int noy = min(geo.nwy * R, AY.n_out - geo.iy0 * R);
         int idl = 0;
-        for (int p = geo.p_first; p <= geo.p_last; ++p, ++job) {
-            const int k = job % S;
+        int rslot = 0;  // ring slot of plane p
+        for (int p = geo.p_first; p <= geo.p_last; ++p) {
             Tin* buf = reinterpret_cast<Tin*>(smem_raw + k * T.buf_bytes);
             // one warp waits for the copy; the barrier releases the others
-            if (threadIdx.x < 32) mbar_wait(&bars[k], (uint32_t)((job / S) & 1), &g_status_fwd3d);
+            if (threadIdx.x < 32) mbar_wait(&bars[k], phase, &g_status_fwd3d);
             __syncthreads();
             const int sd = ext_index(p, AD.n_in, P.pad);
             if (sd < 0) {  // a whole plane of the constant
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
             }
             __syncthreads();
             // ---- pass y: all R rows of a window into the ring slot of plane p
-            float* slot = ring + ((p - geo.p_first) % P.ring) * plane_sz;
+            float* slot = ring + rslot * plane_sz;
             if (col2) {
                 float wf[R][SPAN];
 #pragma unroll
@@ -147,7 +150,6 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
             // ---- pass depth: every window whose planes are all in the ring
             while (idl < geo.nwd && (geo.id0 + idl) * AD.s + AD.lo + AD.span <= p + 1) {
                 const int id = geo.id0 + idl;
-                const int pb = id * AD.s + AD.lo - geo.p_first;
                 const int odb = id * R;
                 if (col2) {
                     float wf[R][SPAN];
@@ -155,9 +157,14 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
                     for (int j = 0; j < R; ++j)
 #pragma unroll
                         for (int q = 0; q < SPAN; ++q) wf[j][q] = sWFd[j * SPAN + q];
+                    // the window completes at plane p: its plane q sits in slot (rslot + 1 + q) mod SPAN
                     const float* rp[SPAN];
 #pragma unroll
-                    for (int q = 0; q < SPAN; ++q) rp[q] = ring + ((pb + q) % P.ring) * plane_sz + oxy;
+                    for (int q = 0; q < SPAN; ++q) {
+                        int sl = rslot + 1 + q;
+                        if (sl >= SPAN) sl -= SPAN;
+                        rp[q] = ring + sl * plane_sz + oxy;
+                    }
                     const long long oplane = (long long)AY.n_out * AX.n_out;
                     Tout* yv = static_cast<Tout*>(P.y) + (long long)geo.plane * AD.n_out * oplane +
                                (long long)geo.iy0 * R * AX.n_out + gox;
@@ -185,6 +192,11 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
             }
             __syncthreads();  // ring slots, sH and this stage are free again
             if (threadIdx.x == 0) issue_next<Tin>(T, cur, t_end, smem_raw, bars);
+            if (++rslot == P.ring) rslot = 0;
+            if (++k == S) {
+                k = 0;
+                phase ^= 1;
+            }
         }
     }
 }

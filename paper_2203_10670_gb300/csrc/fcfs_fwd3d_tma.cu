@@ -11,7 +11,7 @@ namespace fcfs {
 namespace {
 
 template <int NT, typename Tin, typename Tout>
-__global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ TmaFwd3Params T) {
+__global__ void __launch_bounds__(256, 3) fcfs_fwd3d_tma(const __grid_constant__ TmaFwd3Params T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ Cursor3 cur;
     const FwdParams& P = T.P;
@@ -40,11 +40,14 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ Tm
         cur.g = geo3(T, t_begin);
         cur.p = cur.g.p_first;
         cur.n = 0;
+        cur.k = 0;
         for (int k = 0; k < S; ++k) issue_next<Tin>(T, cur, t_end, smem_raw, bars);
     }
     __syncthreads();
     const bool learn = AX.learn || AY.learn || AD.learn;
-    int cur_c = -1, job = 0;
+    int cur_c = -1;
+    int k = 0;           // stage of the current job
+    uint32_t phase = 0;  // its barrier phase
     for (int tile = t_begin; tile < t_end; ++tile) {
         const Geo3 geo = geo3(T, tile);
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
@@ -55,11 +58,11 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ Tm
             cur_c = geo.c;
         }
         int idl = 0;
-        for (int p = geo.p_first; p <= geo.p_last; ++p, ++job) {
-            const int k = job % S;
+        int rslot = 0;  // ring slot of plane p
+        for (int p = geo.p_first; p <= geo.p_last; ++p) {
             Tin* buf = reinterpret_cast<Tin*>(smem_raw + k * T.buf_bytes);
             // one warp waits for the copy; the barrier releases the others
-            if (threadIdx.x < 32) mbar_wait(&bars[k], (uint32_t)((job / S) & 1), &g_status_fwd3d);
+            if (threadIdx.x < 32) mbar_wait(&bars[k], phase, &g_status_fwd3d);
             __syncthreads();
             const int sd = ext_index(p, AD.n_in, P.pad);
             if (sd < 0) {  // a whole plane of the constant
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ Tm
             }
             __syncthreads();
             // ---- y taps into the ring slot of plane p
-            float* slot = ring + ((p - geo.p_first) % P.ring) * plane_sz;
+            float* slot = ring + rslot * plane_sz;
             if (act && ixl < geo.nwx) {
                 for (int jy = 0; jy < AY.r; ++jy) {
                     float w[NT];
@@ -108,7 +111,6 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ Tm
             // ---- depth taps for every window whose planes are all in the ring
             while (idl < geo.nwd && (geo.id0 + idl) * AD.s + AD.lo + AD.span <= p + 1) {
                 const int id = geo.id0 + idl;
-                const int need_lo = id * AD.s + AD.lo;
                 const int odb = id * AD.r;
                 const int gox = geo.ix0 * AX.r + ox;
                 if (act && ixl < geo.nwx && gox < AX.n_out) {
@@ -117,13 +119,17 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ Tm
                     Tout* yv = static_cast<Tout*>(P.y) + (long long)geo.plane * AD.n_out * oplane +
                                (long long)geo.iy0 * AY.r * AX.n_out + gox;
                     for (int jd = 0; jd < AD.r && odb + jd < AD.n_out; ++jd) {
-                        const int pb = need_lo + AD.off[jd] - geo.p_first;
+                        // the window completes at plane p: its plane k sits in slot (rslot + 1 + k) mod ring
+                        const int sb = rslot + 1 + AD.off[jd];
                         float w[NT];
                         const float* rp[NT];
 #pragma unroll
                         for (int t = 0; t < NT; ++t) {
                             w[t] = sWd[jd * NT + t];
-                            rp[t] = ring + ((pb + t) % P.ring) * plane_sz + ox;
+                            int sl = sb + t;
+                            if (sl >= P.ring) sl -= P.ring;
+                            if (sl >= P.ring) sl -= P.ring;
+                            rp[t] = ring + sl * plane_sz + ox;
                         }
                         Tout* yo = yv + (long long)(odb + jd) * oplane;
                         for (int oyl = g; oyl < noy; oyl += G) {
@@ -138,6 +144,11 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ Tm
             }
             __syncthreads();  // ring slots, sH and this stage are free again
             if (threadIdx.x == 0) issue_next<Tin>(T, cur, t_end, smem_raw, bars);
+            if (++rslot == P.ring) rslot = 0;
+            if (++k == S) {
+                k = 0;
+                phase ^= 1;
+            }
         }
     }
 }
@@ -145,6 +156,7 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d_tma(const __grid_constant__ Tm
 template <int NT, typename Tin, typename Tout>
 cudaError_t run3(const TmaFwd3Params& T, cudaStream_t st) {
     const size_t smem = (size_t)T.bar_off + 8 * T.stages;
+    if (T.threads > 256) return cudaErrorInvalidValue;
     auto k = fcfs_fwd3d_tma<NT, Tin, Tout>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -118,6 +118,7 @@ struct Cursor3 {
     int tile;   // tile of the last issued job
     int p;      // plane of the last issued job
     int n;      // jobs issued so far
+    int k;      // stage of the next job to issue
 };
 
 // Issue the next job of the stream [t_begin, t_end) into stage n % stages.
@@ -132,9 +133,9 @@ __device__ __forceinline__ void issue_next(const TmaFwd3Params& T, Cursor3& c, i
             c.p = c.g.p_first;
         }
     }
-    const int k = c.n % T.stages;
-    issue3<Tin>(T, c.g, c.p, reinterpret_cast<Tin*>(smem + k * T.buf_bytes), &bars[k]);
+    issue3<Tin>(T, c.g, c.p, reinterpret_cast<Tin*>(smem + c.k * T.buf_bytes), &bars[c.k]);
     ++c.n;
+    if (++c.k == T.stages) c.k = 0;
 }
 
 }  // namespace

@@ -704,16 +704,18 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
         const size_t gbytes = (size_t)T->GBW * T->GBH * es;
         const size_t obytes = (size_t)T->VYcap * T->QX * 4;
         T->buf_bytes = (int)((std::max(gbytes, obytes) + 127) / 128 * 128);
-        T->fx_off = 2 * T->buf_bytes;
+        T->stages = T->buf_bytes <= 12 * 1024 ? 3 : 2;
+        T->fx_off = T->stages * T->buf_bytes;
         T->w_off = T->fx_off + T->GBH * T->FXP * 4;
-        T->bar_off = (T->w_off + (T->aj[2].s + T->aj[1].s) * w * 4 + 15) / 16 * 16;
-        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 16 <= 56 * 1024) break;
+        T->tab_off = T->w_off + (T->aj[2].s + T->aj[1].s) * w * 4;
+        T->bar_off = (T->tab_off + (T->VXcap + T->VYcap) * 4 + 15) / 16 * 16;
+        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 8 * T->stages <= 56 * 1024) break;
         if (T->QX > 64 && T->QX >= 4 * T->QY) T->QX /= 2;
         else if (T->QY > 8) T->QY /= 2;
         else if (T->QX > 32) T->QX /= 2;
         else break;
     }
-    if (T->GBW > 256 || T->GBH > 256 || T->bar_off + 16 > 200 * 1024) return -1;
+    if (T->GBW > 256 || T->GBH > 256 || T->bar_off + 8 * T->stages > 200 * 1024) return -1;
     T->qtiles_x = (Nx + T->QX - 1) / T->QX;
     T->qtiles_y = (Ny + T->QY - 1) / T->QY;
     T->ntiles = (long long)T->qtiles_x * T->qtiles_y * d->n * d->c;
@@ -738,7 +740,8 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
 
 // Plan the bulk-copy 3D input-gradient kernel (same storage type for g and
 // dx, 16-byte row pitch of g, adjoint taps within the kernel templates).
-// Tiles of 64 (or 32) x 16 real (x, y) indices and a depth chunk sized so the
+// Tiles of up to 128 x 32 real (x, y) indices (a g plane's fixed costs spread
+// over many outputs; two CTAs per SM) and a depth chunk sized so the
 // persistent grid gets several tiles per CTA.
 static int plan_dx3_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, void* gx, TmaDx3Params* T,
                         int* ntk) {
@@ -782,8 +785,8 @@ static int plan_dx3_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, 
             T->nR = 0;
         }
     }
-    T->QX = Nx > 32 ? 64 : 32;
-    T->QY = std::min(16, std::max(1, Ny));
+    T->QX = Nx > 64 ? 128 : Nx > 32 ? 64 : 32;
+    T->QY = std::min(32, std::max(1, Ny));
     const int nfold = T->nL + T->nR;
     for (int it = 0; it < 8; ++it) {
         int vx = 1, vy = 1, gwid = 1, gh = 1;
@@ -818,7 +821,7 @@ static int plan_dx3_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, 
         T->tab_off = (int)off;
         off += (size_t)(T->VXcap + T->VYcap) * 4;
         T->bar_off = (int)((off + 15) / 16 * 16);
-        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 8 * T->stages <= 54 * 1024) break;
+        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 8 * T->stages <= 110 * 1024) break;
         if (T->QY > 8) T->QY /= 2;
         else if (T->QX > 32) T->QX /= 2;
         else break;
@@ -827,7 +830,7 @@ static int plan_dx3_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, 
     T->qtiles_x = (Nx + T->QX - 1) / T->QX;
     T->qtiles_y = (Ny + T->QY - 1) / T->QY;
     const long long base = (long long)T->qtiles_x * T->qtiles_y * d->n * d->c;
-    const long long want = 152LL * 4 * 4;
+    const long long want = 152LL * 2 * 4;
     const long long chunks = std::max(1LL, std::min<long long>(Nd, (want + base - 1) / base));
     T->QD = (int)((Nd + chunks - 1) / chunks);
     T->qtiles_d = (Nd + T->QD - 1) / T->QD;
@@ -1251,6 +1254,7 @@ int prepare_tma3(const fcfs_desc* d, const FwdParams& P, TmaFwd3Params* T, int t
     tma3_sizes(P, es, T);
     if (T->BW > 256 || T->BH > 256) return fail(FCFS_ERR_UNSUPPORTED, "tile too large for one bulk copy");
     T->threads = threads > 0 ? threads : 256;
+    if (T->threads > 256) return fail(FCFS_ERR_UNSUPPORTED, "the volume kernels run 256-thread CTAs");
     if (P.OX > T->threads) return fail(FCFS_ERR_UNSUPPORTED, "tile wider than the CTA");
     if (P.ax[2].nt > 5) return fail(FCFS_ERR_UNSUPPORTED, "3D bulk-copy path takes at most 5 taps per phase");
     const long long nt = (long long)P.tiles_x * P.tiles_y * P.tiles_d * P.planes;

@@ -134,7 +134,8 @@ struct TmaDxParams {
     int GBW, GBH;       // g box (width a multiple of 16 bytes)
     int align;          // g elements per 16 bytes
     int VXcap, VYcap;   // virtual columns / rows a tile may evaluate
-    int buf_bytes, fx_off, w_off, bar_off;
+    int stages;         // g tiles in flight (2..4)
+    int buf_bytes, fx_off, w_off, tab_off, bar_off;
     int threads;
     long long ntiles;
     const void* gy;

@@ -57,6 +57,7 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
                     apply_tiles(P, is3d, t.WX, t.WY, t.WD, t.G);
                     if (!tma && P.OX * P.G > 512) continue;
                     if (tma && is3d) {
+                        if (t.threads > 256) continue;  // the volume kernels run 256-thread CTAs
                         TmaFwd3Params T;
                         if (prepare_tma3(d, P, &T, t.threads) != FCFS_OK || forward3_tma_smem_bytes(T) > 200 * 1024) {
                             clear_error();
