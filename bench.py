@@ -381,6 +381,7 @@ def extras(fcfs, inputs, device, stream, peak, tune=True):
             d5 = fcfs.make_desc(x5.shape, ax, 0, 0)
             fcfs.fcfs_tune_forward(d5, x5.data_ptr(), y5.data_ptr(), stream.cuda_stream, 3)
         t = timed(lambda: fcfs.resize(x5, ax, out=y5), steps, stream) / steps
+        fcfs.resize_backward(None, y5, ax, in_shape=tuple(x5.shape), in_dtype=x5.dtype)  # warm-up
         tdx = timed(lambda: fcfs.resize_backward(None, y5, ax, in_shape=tuple(x5.shape), in_dtype=x5.dtype),
                     steps, stream) / steps
         px = int(np.prod(y5.shape)) // y5.shape[1]

@@ -43,8 +43,9 @@ __device__ __forceinline__ void sts_row(float* p, const float* h) {
     }
 }
 
-// XSPEC: window-per-thread x pass (lanes stride s_x samples, bank-conflict
-// free for odd s_x); otherwise one output column per thread.
+// XSPEC: window-per-thread x pass (lanes stride s_x samples: bank-conflict
+// free for odd s_x, two-way when s_x samples span 8 bytes); otherwise one
+// output column per thread.
 template <int R, int SPAN, typename Tin, typename Tout, int VW, bool XSPEC>
 __global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ TmaFwdParams T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -198,7 +199,10 @@ cudaError_t run_rs(const TmaFwdParams& T, cudaStream_t st) {
     const bool v4 = R * SPAN <= 36 && T.P.OX % 4 == 0 && no % 4 == 0 && y % (4 * sizeof(Tout)) == 0;
     const bool v2 = T.P.OX % 2 == 0 && no % 2 == 0 && y % (2 * sizeof(Tout)) == 0;
     if (!v2) return cudaErrorInvalidValue;
-    const bool xs = (T.P.ax[2].s % 2) == 1 && T.P.WX <= (int)T.threads;
+    // window per thread when lanes' windows (s_x samples apart) hit shared memory
+    // banks at most two ways: odd s_x, or s_x samples within 8 bytes
+    const int sx = T.P.ax[2].s;
+    const bool xs = (sx % 2 == 1 || sx * (int)sizeof(Tin) <= 8) && T.P.WX <= (int)T.threads;
     auto k = v4 ? (xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, true> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, false>)
                 : (xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, true> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
