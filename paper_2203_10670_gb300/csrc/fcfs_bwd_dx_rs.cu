@@ -29,15 +29,14 @@ __device__ __forceinline__ void stage_adj_span(float* WF, const AxisP& A, const 
 // XSPEC: one adjoint window per thread in the x pass (lanes stride r samples:
 // bank-conflict free for odd r); otherwise one intermediate column per thread.
 template <int S, int SPAN, typename Tg, typename Tx, bool XSPEC>
-__global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
+__global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ float sWFx[S * SPAN], sWFy[S * SPAN];
     const AdjP& JX = T.aj[2];
     const AdjP& JY = T.aj[1];
-    unsigned char* const buf0 = smem_raw;
-    unsigned char* const buf1 = smem_raw + T.buf_bytes;
     float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
+    const int NS = T.stages;
     const int QX = T.QX, GBW = T.GBW, FXP = T.FXP, R = JX.r;
     const int Nx = JX.n_x, Ny = JY.n_x;
     // x pass mapping
@@ -48,32 +47,40 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ 
     const int G2 = blockDim.x / QX;
     const int cl = threadIdx.x % QX, g2 = threadIdx.x / QX;
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
     const int ntiles = (int)T.ntiles;
     const int per = (ntiles + gridDim.x - 1) / gridDim.x;
     int tile = blockIdx.x * per;
     const int tile_end = min(ntiles, tile + per);
     if (tile >= tile_end) return;
-    if (threadIdx.x == 0) issue<Tg>(T, dx_geo(T, tile), buf0, &bars[0]);
+    // geometry of the tile in each stage, computed once by the thread that issues its copy
+    __shared__ DxGeo sgeo[4];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+        for (int k = 0; k < NS && tile + k < tile_end; ++k) {
+            sgeo[k] = dx_geo(T, tile + k);
+            issue<Tg>(T, sgeo[k], smem_raw + k * T.buf_bytes, &bars[k]);
+        }
+    }
+    __syncthreads();
     const bool learn = T.ax[2].learn || T.ax[1].learn;
     int cur_c = -1;
-    for (int k = 0; tile < tile_end; ++k, ++tile) {
-        const DxGeo geo = dx_geo(T, tile);
-        const Tg* G0 = reinterpret_cast<const Tg*>((k & 1) ? buf1 : buf0);
-        if (threadIdx.x == 0 && tile + 1 < tile_end)
-            issue<Tg>(T, dx_geo(T, tile + 1), (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
-        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+    int stg = 0;
+    uint32_t phase = 0;
+    for (; tile < tile_end; ++tile) {
+        unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
+        const Tg* G0 = reinterpret_cast<const Tg*>(bufk);
+        // one warp waits for the copy; the barrier releases the others
+        if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
+        __syncthreads();
+        const DxGeo geo = sgeo[stg];
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
+            // the previous tile ended with a barrier: no thread still reads the weights
             stage_adj_span<S, SPAN>(sWFx, T.ax[2], JX, geo.c);
             stage_adj_span<S, SPAN>(sWFy, T.ax[1], JY, geo.c);
             cur_c = geo.c;
+            __syncthreads();
         }
-        __syncthreads();
 
         const int nAX = geo.X.ahi >= geo.X.alo ? geo.X.ahi - geo.X.alo + 1 : 0;
         const int nAY = geo.Y.ahi >= geo.Y.alo ? geo.Y.ahi - geo.Y.alo + 1 : 0;
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ 
         }
         // ---- pass y (adjoint along y) on the tile's real columns
         const bool ypath_smem = geo.Y.left || geo.Y.right || !geo.Y.covered;
-        float* sO = reinterpret_cast<float*>((k & 1) ? buf1 : buf0);  // the g tile is consumed
+        float* sO = reinterpret_cast<float*>(bufk);  // the g tile is consumed
         const int q = geo.qx0 + cl;
         const bool col_ok = g2 < G2 && cl < geo.nqx;
         const bool col_has = col_ok && q <= geo.X.vhi;
@@ -194,13 +201,21 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_rs(const __grid_constant__ 
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();  // sF and this stage are free again
+        if (threadIdx.x == 0 && tile + NS < tile_end) {
+            sgeo[stg] = dx_geo(T, tile + NS);
+            issue<Tg>(T, sgeo[stg], bufk, &bars[stg]);
+        }
+        if (++stg == NS) {
+            stg = 0;
+            phase ^= 1;
+        }
     }
 }
 
 template <int S, int SPAN, typename Tg>
 cudaError_t run_rs(const TmaDxParams& T, cudaStream_t st) {
-    const size_t smem = (size_t)T.bar_off + 16;
+    const size_t smem = (size_t)T.bar_off + 8 * T.stages;
     // measured: the variant pays off when the x pass can own whole windows
     // (odd r, bank-conflict free) and the weight rows stay small; otherwise
     // the per-output kernel is faster
