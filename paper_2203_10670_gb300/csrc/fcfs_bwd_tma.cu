@@ -306,8 +306,9 @@ __device__ __forceinline__ void dw_fix_edges(const TmaDwParams& T, const DwGeo& 
     const int BW = T.BWx;
     if (P.pad == FCFS_PAD_REFLECT) {
         const Tin* xp = static_cast<const Tin*>(x) + (long long)g.plane * H * W;
-        for (int e = threadIdx.x; e < g.rows * BW; e += blockDim.x) {
-            const int ry = e / BW, cx = e - ry * BW;
+        const int BU = min(BW, g.xoff + g.cols);
+        for (int e = threadIdx.x; e < g.rows * BU; e += blockDim.x) {
+            const int ry = e / BU, cx = e - ry * BU;
             const int sy = ext_index(g.row0 + ry, H, P.pad);
             const int sx = ext_index(g.x_al + cx, W, P.pad);
             buf[ry * BW + cx] = xp[(long long)sy * W + sx];
@@ -317,14 +318,16 @@ __device__ __forceinline__ void dw_fix_edges(const TmaDwParams& T, const DwGeo& 
     }
     const bool repl = P.pad == FCFS_PAD_REPLICATE;
     const Tin cv = from_f<Tin>(P.padv);
-    const int cl = max(0, -g.x_al), cr = max(0, g.x_al + BW - W);
+    // only the columns the taps read: [0, xoff + cols) of the box
+    const int BU = min(BW, g.xoff + g.cols);
+    const int cl = min(BU, max(0, -g.x_al)), cr = max(0, g.x_al + BU - W);
     if (cl > 0 || cr > 0) {
         const int ncol = cl + cr;
         for (int e = threadIdx.x; e < g.rows * ncol; e += blockDim.x) {
             const int ry = e / ncol, k = e - ry * ncol;
             const int gy = g.row0 + ry;
             if (gy < 0 || gy >= H) continue;
-            const int cx = k < cl ? k : BW - cr + (k - cl);
+            const int cx = k < cl ? k : BU - cr + (k - cl);
             const int src = (k < cl ? 0 : W - 1) - g.x_al;
             buf[ry * BW + cx] = repl ? buf[ry * BW + src] : cv;
         }
@@ -333,8 +336,8 @@ __device__ __forceinline__ void dw_fix_edges(const TmaDwParams& T, const DwGeo& 
     const int rt = max(0, -g.row0), rb = max(0, g.row0 + g.rows - H);
     if (rt > 0 || rb > 0) {
         const int nrow = rt + rb;
-        for (int e = threadIdx.x; e < nrow * BW; e += blockDim.x) {
-            const int k = e / BW, cx = e - k * BW;
+        for (int e = threadIdx.x; e < nrow * BU; e += blockDim.x) {
+            const int k = e / BU, cx = e - k * BU;
             const int ry = k < rt ? k : g.rows - rb + (k - rt);
             const int src = (k < rt ? 0 : H - 1) - g.row0;
             buf[ry * BW + cx] = repl ? buf[src * BW + cx] : cv;
@@ -388,8 +391,11 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
     const int per = (T.ntiles + gridDim.x - 1) / gridDim.x;
     int tile = blockIdx.x * per;
     const int tile_end = min(T.ntiles, tile + per);
+    // geometry of the tile in each buffer, computed once by the thread that issues its copies
+    __shared__ DwGeo sgeo[2];
     auto issue = [&](int t, int b) {
         const DwGeo g = dw_geo(T, t);
+        sgeo[b] = g;
         fence_proxy_async_smem();
         mbar_expect_tx(&bars[b], tx_bytes);
         tma_load_3d(xb(b), &T.tmap_x, g.x_al, g.row0, g.plane, &bars[b]);
@@ -444,10 +450,13 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
     int seg = 0, cur_c = -1;
     if (tile < tile_end && threadIdx.x == 0) issue(tile, 0);
     for (int k = 0; tile < tile_end; ++k, ++tile) {
-        const DwGeo geo = dw_geo(T, tile);
         Tv* X = xb(k & 1);
         const Tv* Gt = gb(k & 1);
-        if (threadIdx.x == 0 && tile + 1 < tile_end) issue(tile + 1, (k + 1) & 1);
+        // one warp waits for the copies; the barrier releases the others
+        if (threadIdx.x < 32) mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        __syncthreads();
+        const DwGeo geo = sgeo[k & 1];
+        if (threadIdx.x == 0 && tile + 1 < tile_end) issue(tile + 1, (k + 1) & 1);  // the other slot
         const int ch = per_channel ? geo.c : 0;
         if (ch != cur_c) {
             if (cur_c >= 0) flush(seg++, cur_c);
@@ -460,9 +469,8 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
                 sWy[e] = t < AY.nt_src ? (AY.learn ? AY.w[geo.c * AY.w_cstride + j * AY.nt_src + t] : AY.wf[j * AY.nt_src + t]) : 0.f;
             }
             cur_c = ch;
+            __syncthreads();
         }
-        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
-        __syncthreads();
         if (geo.edge) dw_fix_edges<Tv>(T, geo, X, xptr);
 
         // U = x taps of every staged row (thread = output column)
@@ -482,9 +490,12 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
             }
         }
         // V = y taps of every staged column (thread = column and phase)
-        const int ncv = geo.cols * AY.r;
-        for (int p = threadIdx.x; p < ncv; p += blockDim.x) {
-            const int jy = p / geo.cols, cx = p - jy * geo.cols;
+        for (int jy = 0, cx = threadIdx.x; jy < AY.r;) {
+            if (cx >= geo.cols) {
+                cx -= geo.cols;
+                ++jy;
+                continue;
+            }
             float w[NT];
 #pragma unroll
             for (int t = 0; t < NT; ++t) w[t] = sWy[jy * NT + t];
@@ -498,6 +509,7 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
                 src += AY.s * BWx;
                 dst += AY.r * ICp;
             }
+            cx += blockDim.x;
         }
         __syncthreads();
         // dWx: thread = output column, over its group's rows
