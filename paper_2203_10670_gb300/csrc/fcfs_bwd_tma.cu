@@ -549,6 +549,214 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
         for (int s2 = seg; s2 < T.maxseg; ++s2) ids[s2] = -1;
 }
 
+// Register-blocked weight gradient for learnable taps on both axes with the
+// same phase count R and tap count NT (window i of either axis reads x~ at
+// i*s + t, t < NT).  Each pass works per window, so a thread loads a window's
+// samples once and uses them for all R phases:
+//   U  = x taps of x~:   U[row][i*R + jx] = sum_t Wx[jx][t] x~[row][i*s_x + t]
+//   V  = y taps of x~:   V[i*R + jy][col] = sum_t Wy[jy][t] x~[i*s_y + t][col]
+//   dWx[jx][t] += g[oy][i*R + jx] * V[oy][i*s_x + t]     (thread = window, row group)
+//   dWy[jy][t] += g[i*R + jy][ox] * U[i*s_y + t][ox]     (thread = column, window group)
+// Every thread holds all R x NT entries of both axes; a flush reduces them in
+// a fixed order (warp shuffles, then the warps in index order) into the same
+// record layout as the per-output kernel, so the same reduction kernel sums
+// the records.
+template <int R, int NT, typename Tv>
+__global__ void __launch_bounds__(256, 2) fcfs_bwd_dw2d_rb(const __grid_constant__ TmaDwParams T, const void* xptr) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ float sWx[R * NT], sWy[R * NT];
+    __shared__ DwGeo sgeo[2];
+    const FwdParams& P = T.P;
+    const AxisP& AY = P.ax[1];
+    const AxisP& AX = P.ax[2];
+    auto xb = [&](int b) { return reinterpret_cast<Tv*>(smem_raw + b * T.xbuf_bytes); };
+    auto gb = [&](int b) { return reinterpret_cast<Tv*>(smem_raw + 2 * T.xbuf_bytes + b * T.gbuf_bytes); };
+    float* sU = reinterpret_cast<float*>(smem_raw + T.sh_off);   // [rows][OX]
+    float* sV = reinterpret_cast<float*>(smem_raw + T.sv_off);   // [OY][ICp]
+    float* sRed = reinterpret_cast<float*>(smem_raw + T.red_off);  // [warps][2 R NT]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + T.bar_off);
+    constexpr int NE = R * NT;
+    const int OX = P.OX, BWx = T.BWx, BWg = T.BWg, ICp = T.ICp, WX = P.WX;
+    const int SX = AX.s, SY = AY.s;
+    const bool per_channel = AX.w_cstride != 0 || AY.w_cstride != 0;
+    const uint32_t tx_bytes = (uint32_t)(T.BWx * T.BHx + T.BWg * T.BHg) * sizeof(Tv);
+    // thread mappings: window x row group (U, dWx); column x window group (V, dWy)
+    const int GW = blockDim.x / WX;
+    const int iw = threadIdx.x % WX, gw = threadIdx.x / WX;
+    const bool wact = gw < GW;
+
+    float accx[R][NT], accy[R][NT];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) accx[j][t] = accy[j][t] = 0.f;
+
+    float* recs = T.ws + (long long)blockIdx.x * T.maxseg * T.rec;
+    int* ids = reinterpret_cast<int*>(T.ws + (long long)T.grid * T.maxseg * T.rec) + blockIdx.x * T.maxseg;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int per = (T.ntiles + gridDim.x - 1) / gridDim.x;
+    int tile = blockIdx.x * per;
+    const int tile_end = min(T.ntiles, tile + per);
+    auto issue = [&](int t, int b) {
+        const DwGeo g = dw_geo(T, t);
+        sgeo[b] = g;
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bars[b], tx_bytes);
+        tma_load_3d(xb(b), &T.tmap_x, g.x_al, g.row0, g.plane, &bars[b]);
+        tma_load_3d(gb(b), &T.tmap_g, g.g_al, g.iy0 * R, g.plane, &bars[b]);
+    };
+    // reduce every thread's entries into record `seg` for channel c (fixed order)
+    auto flush = [&](int seg, int c) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+        for (int e = 0; e < 2 * NE; ++e) {
+            float v = e < NE ? accx[e / NT][e % NT] : accy[(e - NE) / NT][(e - NE) % NT];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0) sRed[warp * 2 * NE + e] = v;
+        }
+        __syncthreads();
+        float* rec = recs + (long long)seg * T.rec;
+        for (int e = threadIdx.x; e < 2 * NE; e += blockDim.x) {
+            float v = 0.f;
+            for (int w = 0; w < nwarp; ++w) v += sRed[w * 2 * NE + e];
+            // record layout: dWy entries first, then dWx
+            rec[e < NE ? AY.r * NT + e : e - NE] = v;
+        }
+        if (threadIdx.x == 0) ids[seg] = c;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+#pragma unroll
+            for (int t = 0; t < NT; ++t) accx[j][t] = accy[j][t] = 0.f;
+    };
+
+    int seg = 0, cur_c = -1;
+    if (tile < tile_end && threadIdx.x == 0) issue(tile, 0);
+    for (int k = 0; tile < tile_end; ++k, ++tile) {
+        Tv* X = xb(k & 1);
+        const Tv* Gt = gb(k & 1);
+        // one warp waits for the copies; the barrier releases the others
+        if (threadIdx.x < 32) mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        __syncthreads();
+        const DwGeo geo = sgeo[k & 1];
+        if (threadIdx.x == 0 && tile + 1 < tile_end) issue(tile + 1, (k + 1) & 1);  // the other slot
+        const int ch = per_channel ? geo.c : 0;
+        if (ch != cur_c) {
+            if (cur_c >= 0) flush(seg++, cur_c);
+            for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+                sWx[e] = AX.w[geo.c * AX.w_cstride + e];
+                sWy[e] = AY.w[geo.c * AY.w_cstride + e];
+            }
+            cur_c = ch;
+            __syncthreads();
+        }
+        if (geo.edge) dw_fix_edges<Tv>(T, geo, X, xptr);
+
+        // ---- U: x taps of every staged row, a window per thread
+        if (wact && iw < geo.nwx) {
+            float w[R][NT];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+#pragma unroll
+                for (int t = 0; t < NT; ++t) w[j][t] = sWx[j * NT + t];
+            const Tv* src = X + gw * BWx + geo.xoff + iw * SX;
+            float* dst = sU + gw * OX + iw * R;
+            for (int ry = gw; ry < geo.rows; ry += GW) {
+                float v[NT];
+#pragma unroll
+                for (int t = 0; t < NT; ++t) v[t] = to_f<Tv>(src[t]);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    float a = 0.f;
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) a = fmaf(w[j][t], v[t], a);
+                    dst[j] = a;
+                }
+                src += GW * BWx;
+                dst += GW * OX;
+            }
+        }
+        // ---- V: y taps of every staged column, a window per thread step
+        {
+            float w[R][NT];
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+#pragma unroll
+                for (int t = 0; t < NT; ++t) w[j][t] = sWy[j * NT + t];
+            const int GC = blockDim.x / ICp;
+            const int cx = threadIdx.x % ICp, gc = threadIdx.x / ICp;
+            if (gc < GC && cx < geo.cols) {
+                for (int iyl = gc; iyl < geo.nwy; iyl += GC) {
+                    const Tv* src = X + iyl * SY * BWx + geo.xoff + cx;
+                    float v[NT];
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) v[t] = to_f<Tv>(src[t * BWx]);
+                    float* dst = sV + iyl * R * ICp + cx;
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        float a = 0.f;
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) a = fmaf(w[j][t], v[t], a);
+                        dst[j * ICp] = a;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // ---- dWx: a window per thread, over its group's output rows
+        if (wact && iw < geo.nwx) {
+            const int nrow = geo.nwy * R;
+            const Tv* gp = Gt + geo.goff + iw * R;
+            const float* vp = sV + iw * SX;
+            for (int oyl = gw; oyl < nrow; oyl += GW) {
+                float gv[R], v[NT];
+#pragma unroll
+                for (int j = 0; j < R; ++j) gv[j] = to_f<Tv>(gp[oyl * BWg + j]);
+#pragma unroll
+                for (int t = 0; t < NT; ++t) v[t] = vp[oyl * ICp + t];
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) accx[j][t] = fmaf(gv[j], v[t], accx[j][t]);
+            }
+        }
+        // ---- dWy: a column per thread, over its group's windows
+        {
+            const int GO = blockDim.x / OX;
+            const int o = threadIdx.x % OX, go = threadIdx.x / OX;
+            if (go < GO && o / R < geo.nwx) {
+                const Tv* gp = Gt + geo.goff + o;
+                const float* up = sU + o;
+                for (int iyl = go; iyl < geo.nwy; iyl += GO) {
+                    float gv[R], u[NT];
+#pragma unroll
+                    for (int j = 0; j < R; ++j) gv[j] = to_f<Tv>(gp[(iyl * R + j) * BWg]);
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) u[t] = up[(iyl * SY + t) * OX];
+#pragma unroll
+                    for (int j = 0; j < R; ++j)
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) accy[j][t] = fmaf(gv[j], u[t], accy[j][t]);
+                }
+            }
+        }
+        __syncthreads();  // buffers free for the copies two tiles ahead
+    }
+    if (cur_c >= 0) {
+        __syncthreads();
+        flush(seg++, cur_c);
+    }
+    if (threadIdx.x == 0)
+        for (int s2 = seg; s2 < T.maxseg; ++s2) ids[s2] = -1;
+}
+
 // Fixed-order sum of the records of every weight entry (compensated, then a
 // shuffle tree); one warp per entry.
 __global__ void __launch_bounds__(256) fcfs_dw_reduce_tma(const __grid_constant__ TmaDwParams T) {
@@ -592,12 +800,37 @@ __global__ void __launch_bounds__(256) fcfs_dw_reduce_tma(const __grid_constant_
 
 #define FCFS_DW_NT_CASES(X) X(1) X(2) X(3) X(4) X(5) X(7) X(9)
 
+// (R, taps) pairs of the register-blocked weight gradient
+#define FCFS_DW_RB_CASES(X) X(2, 5) X(3, 5) X(4, 5) X(5, 5) X(3, 7) X(5, 7) X(5, 3)
+
+bool dw_rb_compiled(int r, int nt) {
+#define CASE(a, b) \
+    if (r == a && nt == b) return true;
+    FCFS_DW_RB_CASES(CASE)
+#undef CASE
+    return false;
+}
+
 cudaError_t launch_dw_tma(const TmaDwParams& T, int nt, int dt, cudaStream_t st, const void* x) {
     const size_t smem = (size_t)T.bar_off + 16;
     auto go = [&](auto tv) -> cudaError_t {
         using Tv = std::remove_pointer_t<decltype(tv)>;
         cudaError_t e = cudaSuccess;
-        switch (nt) {
+        bool done = false;
+        if (T.rb) {
+#define CASE(a, b)                                                                            \
+    if (!done && T.rb == a && nt == b) {                                                      \
+        auto k = fcfs_bwd_dw2d_rb<a, b, Tv>;                                                  \
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+        if (e != cudaSuccess) return e;                                                       \
+        k<<<T.grid, T.threads, smem, st>>>(T, x);                                             \
+        done = true;                                                                          \
+    }
+            FCFS_DW_RB_CASES(CASE)
+#undef CASE
+            if (!done) return cudaErrorInvalidValue;
+        }
+        if (!done) switch (nt) {
 #define CASE(N)                                                                                          \
     case N: {                                                                                            \
         auto k = fcfs_bwd_dw2d_tma<N, Tv>;                                                               \

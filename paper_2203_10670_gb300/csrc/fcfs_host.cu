@@ -874,8 +874,42 @@ static int plan_dw_tma(const fcfs_desc* d, const FwdParams& P0, const void* x, c
     const int align = 16 / es;
     T->align = align;
     T->threads = 256;
+    // register-blocked kernel: learnable taps on both axes, one phase count and tap count
+    const AxisP &AXx = P.ax[2], &AXy = P.ax[1];
+    T->rb = 0;
+    if (d->ndim == 2 && AXx.learn && AXy.learn && AXx.r == AXy.r && AXx.nt_src == nt && AXy.nt_src == nt &&
+        dw_rb_compiled(AXx.r, nt)) {
+        const int R = AXx.r;
+        int WX = std::max(1, 120 / R), WY = std::max(1, 60 / R);
+        for (int it = 0; it < 64; ++it) {
+            apply_tiles(P, false, WX, WY, 1, 0);
+            T->BWx = (P.IC + align - 1 + align - 1) / align * align;
+            T->BHx = P.IR;
+            T->BWg = (P.OX + align - 1 + align - 1) / align * align;
+            T->BHg = P.OY;
+            T->ICp = P.IC;
+            T->xbuf_bytes = (T->BWx * T->BHx * es + 127) / 128 * 128;
+            T->gbuf_bytes = (T->BWg * T->BHg * es + 127) / 128 * 128;
+            T->sh_off = 2 * T->xbuf_bytes + 2 * T->gbuf_bytes;
+            T->sv_off = T->sh_off + P.IR * P.OX * 4;
+            T->w_off = T->sv_off + P.OY * T->ICp * 4;
+            T->red_off = T->w_off;
+            T->bar_off = (T->red_off + (T->threads / 32) * 2 * R * nt * 4 + 15) / 16 * 16;
+            const bool fits = T->BWx <= 256 && T->BHx <= 256 && T->BWg <= 256 && T->BHg <= 256 &&
+                              P.OX <= T->threads && P.IC <= T->threads && P.WX <= T->threads &&
+                              T->bar_off + 16 <= 110 * 1024;
+            if (fits) {
+                T->rb = R;
+                break;
+            }
+            if ((P.OX > T->threads || P.IC > T->threads || T->BWx > 256) && WX > 1) WX = std::max(1, WX * 3 / 4);
+            else if (WY > 1) WY = (WY + 1) / 2;
+            else if (WX > 1) WX = (WX + 1) / 2;
+            else break;
+        }
+    }
     int WX = std::max(1, 128 / P.ax[2].r), WY = std::max(1, 32 / P.ax[1].r);
-    for (int it = 0; it < 64; ++it) {
+    for (int it = 0; it < 64 && !T->rb; ++it) {
         apply_tiles(P, false, WX, WY, 1, 0);
         const int npair = P.OX * P.ax[1].r;
         T->BWx = (P.IC + align - 1 + align - 1) / align * align;
@@ -899,11 +933,13 @@ static int plan_dw_tma(const fcfs_desc* d, const FwdParams& P0, const void* x, c
         else return -1;
     }
     const int npair = P.OX * P.ax[1].r;
-    if (npair > 2 * T->threads || P.OX > T->threads || T->bar_off + 16 > 227 * 1024) return -1;
+    if (!T->rb && (npair > 2 * T->threads || P.OX > T->threads)) return -1;
+    if (T->bar_off + 16 > 227 * 1024) return -1;
     const long long ntiles = (long long)P.tiles_x * P.tiles_y * P.planes;
     if (ntiles >= (1LL << 31)) return -1;
     T->ntiles = (int)ntiles;
-    const int per_sm = std::max(1, std::min(8, (int)(227 * 1024 / (T->bar_off + 16))));
+    // CTAs per SM by shared memory (the register-blocked kernel is built for two)
+    const int per_sm = std::max(1, std::min(T->rb ? 2 : 8, (int)(227 * 1024 / (T->bar_off + 16))));
     T->grid = (int)std::min<long long>(ntiles, 152LL * per_sm);
     const int per = (T->ntiles + T->grid - 1) / T->grid;
     const int tpp = P.tiles_x * P.tiles_y;

@@ -180,6 +180,7 @@ struct TmaDwParams {
     int ICp;                 // pitch of the V intermediate
     int threads, maxseg, rec;  // CTA size, records per CTA, floats per record
     int ntiles, grid;
+    int rb;                  // phase count of the register-blocked kernel, 0: per-output kernel
     float* ws;               // [grid][maxseg][rec] floats, then [grid][maxseg] plane ids
     float* gw[3];
     long long n;
@@ -307,6 +308,7 @@ cudaError_t launch_forward3d_rs(const TmaFwd3Params& T, int din, int dout, cudaS
 cudaError_t launch_dx3d_tma(const TmaDx3Params& T, int nt, int dt, cudaStream_t st);
 bool dx_rs_compiled(int S, int span);
 cudaError_t launch_dw_tma(const TmaDwParams& T, int nt, int dt, cudaStream_t st, const void* x);
+bool dw_rb_compiled(int r, int nt);
 size_t forward_smem_bytes(const FwdParams& P, bool is3d);
 size_t dx_smem_bytes(const BwdParams& P, bool is3d);
 size_t dw_smem_bytes(const BwdParams& P);

@@ -158,6 +158,27 @@ def test_dw_and_dx_learnable(F, orc, per_channel, ratios, K, pad):
     check_dx(F, orc, tuple(x.shape), axes, pad, seed=6)
 
 
+@pytest.mark.parametrize("per_channel", (True, False))
+@pytest.mark.parametrize("ratio,K", [((5, 4), 2), ((3, 2), 3), ((5, 4), 1), ((4, 3), 2), ((2, 3), 2)])
+@pytest.mark.parametrize("pad", (REPL, CONST, REFL))
+def test_dw_register_blocked(F, orc, per_channel, ratio, K, pad):
+    # learnable taps on both axes with one phase and tap count, 16-byte rows: the
+    # register-blocked weight-gradient kernel (window per thread, all phases at once)
+    C = 3
+    axes = _learn_axes(F, C, (ratio, ratio), K, per_channel, 23)
+    x = inputs.normal((2, C, 41, 144), 11)
+    gshape = (2, C) + tuple((n * ratio[0]) // ratio[1] for n in (41, 144))
+    gy = inputs.normal(gshape, 12)
+    check_dw(F, orc, x, gy, axes, pad, pad_value=0.3 if pad == CONST else 0.0)
+
+
+def test_dw_register_blocked_bf16(F, orc):
+    axes = _learn_axes(F, 4, ((5, 4), (5, 4)), 2, True, 24)
+    x = inputs.normal((2, 4, 37, 256), 13, dtype=torch.bfloat16)
+    gy = inputs.normal((2, 4, 46, 320), 14, dtype=torch.bfloat16)
+    check_dw(F, orc, x, gy, axes, REFL, tol=2e-2)
+
+
 def test_dw_1d(F, orc):
     axes = _learn_axes(F, 4, ((5, 4),), 2, True, 4)
     x = inputs.normal((3, 4, 1001), 7)
