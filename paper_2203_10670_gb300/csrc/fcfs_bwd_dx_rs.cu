@@ -54,12 +54,15 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant
     if (tile >= tile_end) return;
     // geometry of the tile in each stage, computed once by the thread that issues its copy
     __shared__ DxGeo sgeo[4];
+    __shared__ DxWalk walk;  // the next tile to issue
     if (threadIdx.x == 0) {
         for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
+        dx_walk_init(T, walk, tile);
         for (int k = 0; k < NS && tile + k < tile_end; ++k) {
-            sgeo[k] = dx_geo(T, tile + k);
+            sgeo[k] = dx_walk_geo(T, walk);
             issue<Tg>(T, sgeo[k], smem_raw + k * T.buf_bytes, &bars[k]);
+            dx_walk_next(T, walk);
         }
     }
     __syncthreads();
@@ -203,8 +206,9 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant
         }
         __syncthreads();  // sF and this stage are free again
         if (threadIdx.x == 0 && tile + NS < tile_end) {
-            sgeo[stg] = dx_geo(T, tile + NS);
+            sgeo[stg] = dx_walk_geo(T, walk);
             issue<Tg>(T, sgeo[stg], bufk, &bars[stg]);
+            dx_walk_next(T, walk);
         }
         if (++stg == NS) {
             stg = 0;
