@@ -157,6 +157,23 @@ def ncu_traffic(kernel_key):
     return None
 
 
+# ------------------------------------------------------------------ ranks
+
+def slowest_rank(secs, device):
+    """The max over ranks of a local duration (the job is as fast as its slowest replica);
+    the local value when there is no process group."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return secs
+    t = torch.tensor([secs], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, units_per_step, secs):
+    """Whole-job throughput (units per second / 1e9): every rank runs its own replica of the step."""
+    return world * steps * units_per_step / secs / 1e9
+
+
 # ------------------------------------------------------------------ oracle arm
 
 def oracle_sample(steps=1):
@@ -254,12 +271,10 @@ def run_ours(args, rank, world, device):
     if clocks:
         time.sleep(0.2)
     clk = clocks.stop() if clocks else None
+    secs = slowest_rank(secs, device)
     if dist:
-        t = torch.tensor([secs], device=device, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        secs = float(t.item())
         torch.distributed.barrier()
-    value = world * args.steps * pix_step / secs / 1e9
+    value = job_rate(world, args.steps, pix_step, secs)
 
     # per-kernel durations (eager launches with events on the launching stream)
     peak, peak_kind = peaks()
@@ -293,12 +308,8 @@ def run_ours(args, rank, world, device):
     for _ in range(2):
         e2e_step()
     e2e_steps = max(3, args.steps // 4)
-    es = timed(e2e_step, e2e_steps, stream)
-    if dist:
-        t = torch.tensor([es], device=device, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        es = float(t.item())
-    e2e = {"value": world * e2e_steps * pix_step / es / 1e9, "unit": "Gpix/s",
+    es = slowest_rank(timed(e2e_step, e2e_steps, stream), device)
+    e2e = {"value": job_rate(world, e2e_steps, pix_step, es), "unit": "Gpix/s",
            "h2d_bytes_per_step": x.numel() * esz, "d2h_bytes_per_step": sum(v.numel() * esz for v in outs.values())}
 
     line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": args.steps,
