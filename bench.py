@@ -443,7 +443,7 @@ def serve_bench(fcfs, inputs, device, count=None):
         lam = sat["completed"] / max(sat["wall_s"], 1e-9)
         res[f"serve_{tag}_saturation"] = {"req_s": lam, "gpix_s": sat["gpix_s"], "p50_ms": sat["p50_ms"],
                                           "p99_ms": sat["p99_ms"], "steps": sat["steps"]}
-        for frac in (0.5, 0.9):
+        for frac in (0.25, 0.5, 0.75, 0.9, 1.0, 1.25):
             st = run(frac * lam)
             res[f"serve_{tag}_rate{frac:g}"] = {"req_s": frac * lam, "gpix_s": st["gpix_s"], "p50_ms": st["p50_ms"],
                                                 "p99_ms": st["p99_ms"], "deferred": st["deferred"],

@@ -40,10 +40,13 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+ALIGN_PAPER, ALIGN_HALF_PIXEL, ALIGN_FLOOR = 0, 1, 2
+
+
 class _Axis(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int), ("s", ctypes.c_int), ("method", ctypes.c_int),
                 ("K", ctypes.c_int), ("w", ctypes.POINTER(ctypes.c_double)),
-                ("w_per_channel", ctypes.c_int)]
+                ("w_per_channel", ctypes.c_int), ("align", ctypes.c_int), ("cubic_a", ctypes.c_double)]
 
 
 def lib():
@@ -55,6 +58,8 @@ def lib():
         P = ctypes.c_void_p
         L.orc_kernel.restype = d
         L.orc_kernel.argtypes = [i, d]
+        L.orc_kernel_a.restype = d
+        L.orc_kernel_a.argtypes = [i, d, d]
         L.orc_out_len.restype = ll
         L.orc_out_len.argtypes = [ll, i, i]
         L.orc_kmin.argtypes = [i, i]
@@ -118,13 +123,16 @@ def make_weights(method: int, r: int, s: int, K: int = 0):
 # ------------------------------------------------------------------ tensors
 
 def _axes(axes, keep):
-    """axes: list of dicts {r, s, method, K=0, w=None (array [C or 1][r][T] or [r][T])}."""
+    """axes: list of dicts {r, s, method, K=0, w=None (array [C or 1][r][T] or [r][T]),
+    align=ALIGN_PAPER, cubic_a=0 (-1/2)}."""
     arr = (_Axis * len(axes))()
     for k, a in enumerate(axes):
         w = a.get("w")
         arr[k].r, arr[k].s = a["r"], a["s"]
         arr[k].method = a.get("method", BILINEAR)
         arr[k].K = a.get("K", 0)
+        arr[k].align = a.get("align", ALIGN_PAPER)
+        arr[k].cubic_a = float(a.get("cubic_a", 0.0))
         if w is not None:
             w = np.ascontiguousarray(w, dtype=np.float64)
             keep.append(w)

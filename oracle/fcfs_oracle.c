@@ -20,6 +20,11 @@
  *   - output o samples the input at p = o s / r             [Sec. 3.2: phase j of window i at i + j/r, stride units]
  *   - direct formula: y(p) = sum_t k(p - t) x~[t]           [Sec. 5.2, bilinear and Keys kernels]
  *     nearest: x~[floor(p + 1/2)] in exact integers         [Sec. 5.2.1 examples: rounding, ties upward]
+ *   - sample-alignment variants (not the paper's; the conventions of common
+ *     resize libraries), fixed methods only:
+ *       half-pixel centres p = (o + 1/2) s / r - 1/2, nearest x~[floor((o + 1/2) s / r)]
+ *       floor nearest x~[floor(o s / r)] (linear/cubic as the paper's p)
+ *     and the Keys parameter a (the paper's kernel has a = -1/2).
  *   - polyphase form with explicit weights W[j][m]:
  *     y[i r + j] = sum_m W[j][m] x~[i s - L + m]            [Sec. 3.2 pseudocode: pad, conv(stride s, r outputs), pixelshuffle]
  *     window half width K >= K_min, T = 2K + 1, L = K - floor(s/2)
@@ -41,6 +46,7 @@
 
 enum { ORC_NEAREST = 0, ORC_BILINEAR = 1, ORC_BICUBIC = 2 };
 enum { ORC_PAD_REPLICATE = 0, ORC_PAD_CONSTANT = 1, ORC_PAD_REFLECT = 2 };
+enum { ORC_ALIGN_PAPER = 0, ORC_ALIGN_HALF_PIXEL = 1, ORC_ALIGN_FLOOR = 2 };
 
 typedef struct {
     int r, s;         /* scale factor r/s on this axis */
@@ -48,6 +54,8 @@ typedef struct {
     int K;            /* polyphase half width, T = 2K+1; 0 -> K_min(method, s) */
     const double* w;  /* polyphase weights [C or 1][r][T]; NULL -> the method's table */
     int w_per_channel;
+    int align;        /* ORC_ALIGN_*: sample positions of the fixed methods */
+    double cubic_a;   /* Keys parameter of bicubic; 0 -> -1/2 */
 } orc_axis;
 
 int orc_num_threads(void) {
@@ -63,17 +71,18 @@ int orc_num_threads(void) {
 /* Interpolation kernel of Sec. 5.2.  Bilinear: the hat max(0, 1-|t|).
  * Bicubic: Keys' cubic convolution kernel with a = -0.5, whose constant term
  * -4a on 1<|t|<2 is +2. Nearest has no continuous kernel here (NAN). */
-double orc_kernel(int method, double t) {
+double orc_kernel_a(int method, double t, double ka) {
     double a = fabs(t);
     if (method == ORC_BILINEAR) return a < 1.0 ? 1.0 - a : 0.0;
     if (method == ORC_BICUBIC) {
-        const double ka = -0.5;
         if (a <= 1.0) return (ka + 2.0) * a * a * a - (ka + 3.0) * a * a + 1.0;
         if (a < 2.0) return ka * a * a * a - 5.0 * ka * a * a + 8.0 * ka * a - 4.0 * ka;
         return 0.0;
     }
     return NAN;
 }
+
+double orc_kernel(int method, double t) { return orc_kernel_a(method, t, -0.5); }
 
 /* support radius R: the kernel is zero for |t| >= R (nearest picks one of 2 taps) */
 int orc_support(int method) { return method == ORC_BICUBIC ? 2 : 1; }
@@ -137,8 +146,13 @@ int orc_make_weights(int method, int r, int s, int K, double* w) {
 typedef struct {
     long long n_in, n_out, n_win;
     int r, s, method, K, T, L, per_channel;
+    int align;       /* ORC_ALIGN_* (fixed methods) */
+    double cubic_a;  /* Keys parameter */
     const double* w; /* polyphase weights (may be the method table) */
 } axis_t;
+
+/* the fixed-method table of this axis describes it exactly (paper alignment, a = -1/2) */
+static int table_exact(const axis_t* A) { return A->align == ORC_ALIGN_PAPER && A->cubic_a == -0.5; }
 
 #define MAXTAP 256
 
@@ -152,6 +166,7 @@ static int setup_axes(int ndim, const long long* in_shape, const orc_axis* ax, a
         if (a < lead) { /* identity axis of extent 1 */
             A->n_in = 1; A->r = 1; A->s = 1; A->method = ORC_NEAREST;
             A->K = 0; A->T = 1; A->L = 0; A->per_channel = 0;
+            A->align = ORC_ALIGN_PAPER; A->cubic_a = -0.5;
             tables[a] = (double*)malloc(sizeof(double));
             tables[a][0] = 1.0;
             A->w = tables[a];
@@ -164,6 +179,9 @@ static int setup_axes(int ndim, const long long* in_shape, const orc_axis* ax, a
             if (A->T > MAXTAP) return -1;
             A->L = orc_left_offset(A->K, A->s);
             A->per_channel = g->w ? g->w_per_channel : 0;
+            if (g->align < ORC_ALIGN_PAPER || g->align > ORC_ALIGN_FLOOR) return -1;
+            A->align = g->align;
+            A->cubic_a = g->cubic_a != 0.0 ? g->cubic_a : -0.5;
             if (g->w) {
                 A->w = g->w;
             } else {
@@ -182,20 +200,31 @@ static void free_tables(double* tables[3]) {
     for (int a = 0; a < 3; ++a) free(tables[a]);
 }
 
-/* taps of the direct formula at output o: sample p = o s / r */
+/* taps of the direct formula at output o.  The sample position is the exact
+ * rational p = num / den:
+ *   paper (and floor)  p = o s / r                 num = o s,           den = r
+ *   half-pixel         p = (o + 1/2) s / r - 1/2   num = 2 o s + s - r,  den = 2 r
+ * nearest: paper floor(p + 1/2), floor floor(o s / r), half-pixel floor((o + 1/2) s / r) */
 static int taps_direct(const axis_t* A, long long o, long long* t, double* w) {
     long long os = o * (long long)A->s;
     if (A->method == ORC_NEAREST) {
-        t[0] = orc_floor_div(2 * os + A->r, 2LL * A->r); /* floor(p + 1/2) */
+        if (A->align == ORC_ALIGN_FLOOR) t[0] = orc_floor_div(os, A->r);
+        else if (A->align == ORC_ALIGN_HALF_PIXEL) t[0] = orc_floor_div(2 * os + A->s, 2LL * A->r);
+        else t[0] = orc_floor_div(2 * os + A->r, 2LL * A->r); /* floor(p + 1/2) */
         w[0] = 1.0;
         return 1;
     }
+    long long num = os, den = A->r;
+    if (A->align == ORC_ALIGN_HALF_PIXEL) {
+        num = 2 * os + A->s - A->r;
+        den = 2LL * A->r;
+    }
     int R = orc_support(A->method);
-    long long b = orc_floor_div(os, A->r); /* floor(p) */
+    long long b = orc_floor_div(num, den); /* floor(p) */
     int n = 0;
     for (long long q = b - R + 1; q <= b + R; ++q) {
         t[n] = q;
-        w[n] = orc_kernel(A->method, (double)(os - q * A->r) / (double)A->r); /* k(p - q) */
+        w[n] = orc_kernel_a(A->method, (double)(num - q * den) / (double)den, A->cubic_a); /* k(p - q) */
         ++n;
     }
     return n;
@@ -262,6 +291,11 @@ static int resize(int poly, int ndim, long long n, long long c, const long long*
         free_tables(tables);
         return -1;
     }
+    for (int a = 0; poly && a < 3; ++a)
+        if (tables[a] && !table_exact(&ax[a])) { /* the method table is the paper's */
+            free_tables(tables);
+            return -1;
+        }
     long long in_plane = ax[0].n_in * ax[1].n_in * ax[2].n_in;
     long long out_plane = ax[0].n_out * ax[1].n_out * ax[2].n_out;
     long long planes = n * c;
@@ -331,6 +365,8 @@ int orc_adjoint_dx(int ndim, long long n, long long c, const long long* in_shape
         free_tables(tables);
         return -1;
     }
+    int direct[3];
+    for (int a = 0; a < 3; ++a) direct[a] = tables[a] != NULL && !table_exact(&ax[a]);
     long long in_plane = ax[0].n_in * ax[1].n_in * ax[2].n_in;
     long long out_plane = ax[0].n_out * ax[1].n_out * ax[2].n_out;
     long long planes = n * c;
@@ -346,9 +382,11 @@ int orc_adjoint_dx(int ndim, long long n, long long c, const long long* in_shape
             for (long long o1 = 0; o1 < ax[1].n_out; ++o1)
                 for (long long o2 = 0; o2 < ax[2].n_out; ++o2) {
                     double gv = gp[(o0 * ax[1].n_out + o1) * ax[2].n_out + o2];
-                    int n0 = taps_poly(&ax[0], o0, ch, t0, w0);
-                    int n1 = taps_poly(&ax[1], o1, ch, t1, w1);
-                    int n2 = taps_poly(&ax[2], o2, ch, t2, w2);
+                    /* the polyphase taps, or the direct ones where a fixed method's
+                     * alignment / Keys parameter is not its table's */
+                    int n0 = direct[0] ? taps_direct(&ax[0], o0, t0, w0) : taps_poly(&ax[0], o0, ch, t0, w0);
+                    int n1 = direct[1] ? taps_direct(&ax[1], o1, t1, w1) : taps_poly(&ax[1], o1, ch, t1, w1);
+                    int n2 = direct[2] ? taps_direct(&ax[2], o2, t2, w2) : taps_poly(&ax[2], o2, ch, t2, w2);
                     for (int a = 0; a < n0; ++a) {
                         long long q0 = orc_ext_index(t0[a], ax[0].n_in, pad);
                         if (q0 < 0) continue;
@@ -410,6 +448,11 @@ int orc_adjoint_dx_at(int ndim, long long n, long long c, const long long* in_sh
         free_tables(tables);
         return -1;
     }
+    for (int a = 0; a < 3; ++a)
+        if (tables[a] && !table_exact(&ax[a])) { /* gathered from the paper's tables only */
+            free_tables(tables);
+            return -1;
+        }
     long long in_plane = ax[0].n_in * ax[1].n_in * ax[2].n_in;
     long long out_plane = ax[0].n_out * ax[1].n_out * ax[2].n_out;
     int bad = 0;

@@ -581,3 +581,100 @@ def test_shared_weight_gradient_sums_channels(orc):
     dp = orc.weight_grad(x, g, per)
     for a in range(2):
         assert np.allclose(ds[a], dp[a].sum(0), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------- sample-alignment variants (P5)
+# Not the paper's sampling: the half-pixel-centre and floor-nearest conventions of
+# common resize libraries.  Pinned to PyTorch's CPU interpolation in float64, which
+# uses the same positions when given scale_factor (not size).
+
+HALF, FLOOR = 1, 2
+VAR_RATIOS = [(3, 2), (2, 3), (4, 3), (5, 4), (7, 5), (5, 2), (1, 2), (2, 1), (2, 11)]
+
+
+def _torch_interp(x, ratio, mode, ndim):
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    sf = (ratio[0] / ratio[1],) * ndim
+    kw = {} if mode in ("nearest", "nearest-exact") else {"align_corners": False}
+    return F.interpolate(torch.from_numpy(x), scale_factor=sf, mode=mode, recompute_scale_factor=False, **kw).numpy()
+
+
+@pytest.mark.parametrize("ratio", VAR_RATIOS)
+def test_half_pixel_bilinear_matches_library_interpolation(orc, ratio):
+    x = np.random.default_rng(41).random((1, 2, 13, 17))
+    want = _torch_interp(x, ratio, "bilinear", 2)
+    got = orc.resize(x, [dict(r=ratio[0], s=ratio[1], method=BILINEAR, align=HALF)] * 2, pad=REPL)
+    assert got.shape == want.shape
+    assert np.abs(got - want).max() <= 1e-12
+
+
+@pytest.mark.parametrize("ratio", VAR_RATIOS)
+def test_half_pixel_bicubic_a075_matches_library_interpolation(orc, ratio):
+    # the library's cubic has Keys a = -3/4 and clamps indices at the border (replicate)
+    x = np.random.default_rng(42).random((1, 2, 13, 17))
+    want = _torch_interp(x, ratio, "bicubic", 2)
+    got = orc.resize(x, [dict(r=ratio[0], s=ratio[1], method=BICUBIC, align=HALF, cubic_a=-0.75)] * 2, pad=REPL)
+    assert got.shape == want.shape
+    assert np.abs(got - want).max() <= 1e-12
+
+
+@pytest.mark.parametrize("ratio", VAR_RATIOS)
+@pytest.mark.parametrize("align,mode", [(FLOOR, "nearest"), (HALF, "nearest-exact")])
+def test_nearest_variants_match_library_interpolation(orc, ratio, align, mode):
+    x = np.random.default_rng(43).random((2, 1, 11, 19))
+    want = _torch_interp(x, ratio, mode, 2)
+    got = orc.resize(x, [dict(r=ratio[0], s=ratio[1], method=NEAREST, align=align)] * 2, pad=REPL)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("ratio", [(3, 2), (2, 3), (5, 4)])
+def test_half_pixel_linear_1d_matches_library_interpolation(orc, ratio):
+    x = np.random.default_rng(44).random((1, 3, 29))
+    want = _torch_interp(x, ratio, "linear", 1)
+    got = orc.resize(x, [dict(r=ratio[0], s=ratio[1], method=BILINEAR, align=HALF)], pad=REPL)
+    assert np.abs(got - want).max() <= 1e-12
+
+
+def test_floor_nearest_s1_is_repeat_interleave(orc):
+    # floor-nearest at r/1 repeats every sample r times (the paper's rounding does not)
+    x = np.random.default_rng(45).random((1, 1, 9))
+    for r in (2, 3, 4):
+        got = orc.resize(x, [dict(r=r, s=1, method=NEAREST, align=FLOOR)])
+        assert np.array_equal(got[0, 0], np.repeat(x[0, 0], r))
+
+
+@pytest.mark.parametrize("method", (BILINEAR, BICUBIC))
+def test_variant_invariants(orc, method):
+    rng = np.random.default_rng(46)
+    x = rng.random((1, 1, 12, 10))
+    # r = s: the half-pixel position is the sample itself
+    same = orc.resize(x, [dict(r=3, s=3, method=method, align=HALF)] * 2)
+    assert np.abs(same - x).max() <= 1e-15
+    # floor alignment only changes nearest
+    a = orc.resize(x, [dict(r=4, s=3, method=method, align=FLOOR)] * 2)
+    b = orc.resize(x, [dict(r=4, s=3, method=method)] * 2)
+    assert np.array_equal(a, b)
+    # constants are preserved, any Keys parameter
+    c = np.full((1, 1, 8, 8), 0.37)
+    for ka in (-0.5, -0.75):
+        y = orc.resize(c, [dict(r=5, s=4, method=method, align=HALF, cubic_a=ka)] * 2, pad=REFL)
+        assert np.abs(y - 0.37).max() <= 1e-14
+    # the polyphase evaluation refuses fixed-method variants (its tables are the paper's)
+    with pytest.raises(ValueError):
+        orc.resize(x, [dict(r=4, s=3, method=method, align=HALF)] * 2, polyphase=True)
+
+
+@pytest.mark.parametrize("pad", (REPL, CONST, REFL))
+@pytest.mark.parametrize("axes", [[dict(r=3, s=2, method=BICUBIC, align=HALF, cubic_a=-0.75)] * 2,
+                                  [dict(r=2, s=3, method=BILINEAR, align=HALF), dict(r=5, s=4, method=NEAREST, align=FLOOR)],
+                                  [dict(r=4, s=3, method=NEAREST, align=HALF)] * 2])
+def test_variant_adjoint_dot_product(orc, pad, axes):
+    rng = np.random.default_rng(47)
+    x = rng.standard_normal((2, 2, 9, 11))
+    y = orc.resize(x, axes, pad=pad, pad_value=0.0)
+    g = rng.standard_normal(y.shape)
+    dx = orc.adjoint_dx(g, (9, 11), axes, pad=pad)
+    lhs, rhs = np.vdot(y, g), np.vdot(x, dx)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.abs(y).sum())
