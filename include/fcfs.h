@@ -56,8 +56,17 @@ typedef enum { FCFS_NEAREST = 0, FCFS_BILINEAR = 1, FCFS_BICUBIC = 2 } fcfs_meth
  * distance by periodic mirroring with period 2(N-1)). */
 typedef enum { FCFS_PAD_REPLICATE = 0, FCFS_PAD_CONSTANT = 1, FCFS_PAD_REFLECT = 2 } fcfs_pad;
 
-/* Sample alignment: only the paper's p = o s / r is implemented. */
-typedef enum { FCFS_ALIGN_PAPER = 0 } fcfs_align;
+/* Sample alignment of the fixed methods (learnable weights define their own
+ * taps and ignore it):
+ *   FCFS_ALIGN_PAPER       output o samples p = o s / r (Sec. 3.2: phase j of
+ *                          window i at offset i + j/r in stride units); nearest
+ *                          takes floor(p + 1/2) (Sec. 5.2.1 examples)
+ *   FCFS_ALIGN_HALF_PIXEL  pixel centres: p = (o + 1/2) s / r - 1/2; nearest
+ *                          takes floor((o + 1/2) s / r)
+ *   FCFS_ALIGN_FLOOR       p = o s / r; nearest takes floor(p)
+ * The last two are the conventions of common resize libraries, not the
+ * paper's; every one of them is still a period-r polyphase operator. */
+typedef enum { FCFS_ALIGN_PAPER = 0, FCFS_ALIGN_HALF_PIXEL = 1, FCFS_ALIGN_FLOOR = 2 } fcfs_align;
 
 /* Element types.  FCFS_U8 is accepted as an input type (converted exactly to
  * FP32 at load).  Arithmetic is FP32 everywhere; BF16 is a storage format
@@ -109,8 +118,10 @@ typedef struct {
     int dtype_out;           /* fcfs_dtype of y (F32, BF16) */
     int pad;                 /* fcfs_pad */
     float pad_value;         /* constant for FCFS_PAD_CONSTANT */
-    int align;               /* FCFS_ALIGN_PAPER */
+    int align;               /* fcfs_align of the fixed methods */
     fcfs_axis axis[3];       /* same order as in_shape */
+    float cubic_a;           /* Keys parameter of the fixed bicubic: 0 selects the
+                                paper's -0.5 (Sec. 5.2); -0.75 is another common choice */
 } fcfs_desc;
 
 /*

@@ -24,7 +24,8 @@ FCFS_ERR_BUSY = -7
 FCFS_NEAREST, FCFS_BILINEAR, FCFS_BICUBIC = 0, 1, 2
 # fcfs_pad
 FCFS_PAD_REPLICATE, FCFS_PAD_CONSTANT, FCFS_PAD_REFLECT = 0, 1, 2
-FCFS_ALIGN_PAPER = 0
+# fcfs_align
+FCFS_ALIGN_PAPER, FCFS_ALIGN_HALF_PIXEL, FCFS_ALIGN_FLOOR = 0, 1, 2
 # fcfs_dtype
 FCFS_F32, FCFS_BF16, FCFS_U8 = 0, 1, 2
 FCFS_MAX_R = 64
@@ -40,7 +41,8 @@ class fcfs_desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_longlong), ("c", ctypes.c_longlong),
                 ("in_shape", ctypes.c_longlong * 3), ("out_shape", ctypes.c_longlong * 3),
                 ("dtype_in", ctypes.c_int), ("dtype_out", ctypes.c_int), ("pad", ctypes.c_int),
-                ("pad_value", ctypes.c_float), ("align", ctypes.c_int), ("axis", fcfs_axis * 3)]
+                ("pad_value", ctypes.c_float), ("align", ctypes.c_int), ("axis", fcfs_axis * 3),
+                ("cubic_a", ctypes.c_float)]
 
 
 class fcfs_serve_config(ctypes.Structure):

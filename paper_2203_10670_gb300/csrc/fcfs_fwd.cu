@@ -119,10 +119,20 @@ __global__ void __launch_bounds__(512) fcfs_fwd3d(const __grid_constant__ FwdPar
     }
 }
 
-// Nearest on every axis: y[o] = x~[floor((2 o s + r) / (2 r))] per axis, an
-// exact copy (round half up, Sec. 5.2.1 examples).  One block covers OYT x OXT
+// Nearest on every axis: y[o] = x~[src(o)] per axis (the paper's rule rounds
+// o s / r half up, Sec. 5.2.1 examples; see nearest_src for the others), an
+// exact copy.  One block covers OYT x OXT
 // outputs of one (plane, output depth) slice; source indices come from small
 // shared-memory maps.
+// Source of nearest output o (non-negative integers only): the paper's
+// position o s / r rounded half up, rounded down (floor alignment), or the
+// pixel centre (o + 1/2) s / r rounded down (half-pixel alignment).
+__device__ __forceinline__ int nearest_src(long long o, int r, int s, int align) {
+    if (align == FCFS_ALIGN_FLOOR) return (int)(o * s / r);
+    if (align == FCFS_ALIGN_HALF_PIXEL) return (int)((2 * o * s + s) / (2LL * r));
+    return (int)((2 * o * s + r) / (2LL * r));
+}
+
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) fcfs_nearest(const __grid_constant__ NearestParams P) {
     __shared__ int colmap[256];
@@ -136,16 +146,12 @@ __global__ void __launch_bounds__(256) fcfs_nearest(const __grid_constant__ Near
     const long long plane = t / P.n_out[0];
     const int ox0 = tx * P.OXT, oy0 = ty * P.OYT;
     const int ncol = min(P.OXT, P.n_out[2] - ox0), nrow = min(P.OYT, P.n_out[1] - oy0);
-    for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
-        const long long o = ox0 + k;
-        colmap[k] = ext_index((int)((2 * o * P.s[2] + P.r[2]) / (2LL * P.r[2])), P.n_in[2], P.pad);
-    }
-    for (int k = threadIdx.x; k < nrow; k += blockDim.x) {
-        const long long o = oy0 + k;
-        rowmap[k] = ext_index((int)((2 * o * P.s[1] + P.r[1]) / (2LL * P.r[1])), P.n_in[1], P.pad);
-    }
+    for (int k = threadIdx.x; k < ncol; k += blockDim.x)
+        colmap[k] = ext_index(nearest_src(ox0 + k, P.r[2], P.s[2], P.align), P.n_in[2], P.pad);
+    for (int k = threadIdx.x; k < nrow; k += blockDim.x)
+        rowmap[k] = ext_index(nearest_src(oy0 + k, P.r[1], P.s[1], P.align), P.n_in[1], P.pad);
     __syncthreads();
-    const int sd = ext_index((int)((2LL * od * P.s[0] + P.r[0]) / (2LL * P.r[0])), P.n_in[0], P.pad);
+    const int sd = ext_index(nearest_src(od, P.r[0], P.s[0], P.align), P.n_in[0], P.pad);
     const long long in_plane = (long long)P.n_in[1] * P.n_in[2];
     const Tin* xp = static_cast<const Tin*>(P.x) + (plane * P.n_in[0] + (sd < 0 ? 0 : sd)) * in_plane;
     Tout* yp = static_cast<Tout*>(P.y) + ((plane * P.n_out[0] + od) * (long long)P.n_out[1] + oy0) * P.n_out[2] + ox0;

@@ -1,6 +1,8 @@
 // libfcfs host side: the C ABI entry points, argument validation, the weight
 // and geometry tables of Sec. 3.2 / Sec. 5.2, and the tile planner.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -36,16 +38,18 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 // Interpolation kernels of Sec. 5.2 evaluated in FP64: the bilinear hat and
 // Keys' cubic convolution kernel with a = -1/2.
-double kernel_value(int method, double t) {
+double kernel_value(int method, double t, double ka) {
     const double a = fabs(t);
     if (method == FCFS_BILINEAR) return a < 1.0 ? 1.0 - a : 0.0;
-    const double ka = -0.5;
     if (a <= 1.0) return ((ka + 2.0) * a - (ka + 3.0)) * a * a + 1.0;
     if (a < 2.0) return ((ka * a - 5.0 * ka) * a + 8.0 * ka) * a - 4.0 * ka;
     return 0.0;
 }
 
 int support_radius(int method) { return method == FCFS_BICUBIC ? 2 : 1; }
+
+// Keys parameter of a descriptor: 0 selects the paper's -0.5
+double keys_a(const fcfs_desc* d) { return d->cubic_a != 0.f ? (double)d->cubic_a : -0.5; }
 
 int k_min(int method, int s) { return (s + 2 * support_radius(method) - 2 + 1) / 2; }
 
@@ -66,23 +70,34 @@ int template_taps(int nt) {
 }
 
 // Fixed-method phase table in compact form: for phase j the taps sit at
-// i*s + first_j + t relative to window i.  The sample of phase j is at
-// f_j = j s / r past i*s; the kernel is evaluated at (j s - q r) / r.
-static void fixed_phase(int method, int r, int s, int j, int* first, double* w, int* nt) {
-    const long long num = (long long)j * s;
-    const long long b = num / r;
+// i*s + first_j + t relative to window i.  Phase j samples the rational
+// position num/den past i*s: j s / r (paper and floor alignment) or
+// (2 j s + s - r) / (2 r) (half-pixel centres); the kernel is evaluated at
+// (num - q den) / den for tap q.  Nearest rounds the paper's position half up,
+// the floor alignment's down, and takes floor((2 j s + s) / (2 r)) for
+// half-pixel centres.
+static void fixed_phase(int method, int r, int s, int j, int align, double ka, int* first, double* w, int* nt) {
     if (method == FCFS_NEAREST) {
-        *first = (int)((2 * num + r) / (2LL * r));
+        const long long js = (long long)j * s;
+        if (align == FCFS_ALIGN_FLOOR) *first = (int)(js / r);
+        else if (align == FCFS_ALIGN_HALF_PIXEL) *first = (int)((2 * js + s) / (2LL * r));
+        else *first = (int)((2 * js + r) / (2LL * r));
         w[0] = 1.0;
         *nt = 1;
         return;
     }
+    long long num = (long long)j * s, den = r;
+    if (align == FCFS_ALIGN_HALF_PIXEL) {
+        num = 2LL * j * s + s - r;
+        den = 2LL * r;
+    }
+    const long long b = floor_div(num, den);
     const int R = support_radius(method);
     *first = (int)(b - R + 1);
     *nt = 2 * R;
     for (int t = 0; t < 2 * R; ++t) {
         const long long q = b - R + 1 + t;
-        w[t] = kernel_value(method, (double)(num - q * r) / (double)r);
+        w[t] = kernel_value(method, (double)(num - q * den) / (double)den, ka);
     }
 }
 
@@ -112,7 +127,8 @@ int validate_desc(const fcfs_desc* d, bool output_dtype_check) {
     if (output_dtype_check && d->dtype_out != FCFS_F32 && d->dtype_out != FCFS_BF16)
         return fail(FCFS_ERR_ARG, "dtype_out must be F32 or BF16 (got %d)", d->dtype_out);
     if (d->pad < FCFS_PAD_REPLICATE || d->pad > FCFS_PAD_REFLECT) return fail(FCFS_ERR_ARG, "unknown pad mode %d", d->pad);
-    if (d->align != FCFS_ALIGN_PAPER) return fail(FCFS_ERR_UNSUPPORTED, "only FCFS_ALIGN_PAPER is implemented");
+    if (d->align < FCFS_ALIGN_PAPER || d->align > FCFS_ALIGN_FLOOR) return fail(FCFS_ERR_ARG, "unknown alignment %d", d->align);
+    if (!std::isfinite(d->cubic_a)) return fail(FCFS_ERR_ARG, "cubic_a must be finite");
     if (d->c > INT_MAX) return fail(FCFS_ERR_ARG, "c too large");
     for (int a = 0; a < d->ndim; ++a) {
         int rc = validate_axis(d->axis[a], a);
@@ -144,7 +160,7 @@ int dtype_size(int dt) { return dt == FCFS_F32 ? 4 : dt == FCFS_BF16 ? 2 : 1; }
 
 // Fill the compact polyphase form of one real axis; nt_kernel is the
 // template width every phase is evaluated with (zero-padded taps).
-void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel) {
+void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel, int align, double ka) {
     memset(A, 0, sizeof(*A));
     A->r = a.r;
     A->s = a.s;
@@ -167,7 +183,7 @@ void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kerne
     double w[kMaxFixedTaps];
     int lo = INT_MAX, nt = 1;
     for (int j = 0; j < a.r; ++j) {
-        fixed_phase(a.method, a.r, a.s, j, &first[j], w, &nt);
+        fixed_phase(a.method, a.r, a.s, j, align, ka, &first[j], w, &nt);
         lo = std::min(lo, first[j]);
         for (int t = 0; t < nt; ++t) A->wf[j * nt + t] = (float)w[t];
     }
@@ -199,7 +215,7 @@ void identity_axis(AxisP* A, int nt_kernel) {
 // ----------------------------------------------------------- tile planning
 
 struct PlanKey {
-    int ndim, r[3], s[3], nt, din, dout;
+    int ndim, r[3], s[3], nt, din, dout, lo[3], span[3];
     bool operator==(const PlanKey& o) const { return memcmp(this, &o, sizeof(PlanKey)) == 0; }
 };
 struct PlanKeyHash {
@@ -224,6 +240,7 @@ static PlanKey plan_key(const FwdParams& P, int ndim, int din, int dout) {
     k.nt = P.ax[2].nt;
     k.din = din;
     k.dout = dout;
+    for (int a = 0; a < 3; ++a) k.lo[a] = P.ax[a].lo, k.span[a] = P.ax[a].span;  // alignment moves the taps
     return k;
 }
 
@@ -344,7 +361,7 @@ int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out)
     for (int j = 0; j < r; ++j) {
         int first, nt;
         double w[kMaxFixedTaps];
-        fixed_phase(method, r, s, j, &first, w, &nt);
+        fixed_phase(method, r, s, j, FCFS_ALIGN_PAPER, -0.5, &first, w, &nt);
         for (int m = 0; m < T; ++m) w_out[j * T + m] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const int m = first + t + L;  // tap offset first+t from i*s, window origin i*s - L
@@ -397,6 +414,7 @@ int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
         P.planes = d->n * d->c;
         P.pad = d->pad;
         P.padv = d->pad_value;
+        P.align = d->align;
         P.OXT = P.n_out[2] >= 256 ? 256 : P.n_out[2] > 64 ? 128 : P.n_out[2] > 32 ? 64 : 32;
         P.OYT = std::min(64, 2048 / P.OXT);
         P.tiles_x = (P.n_out[2] + P.OXT - 1) / P.OXT;
@@ -437,7 +455,7 @@ int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* 
     const int lead = 3 - d->ndim;
     for (int a = 0; a < 3; ++a) {
         if (a < lead) identity_axis(&P.ax[a], w);
-        else fill_axis(&P.ax[a], d->axis[a - lead], d->in_shape[a - lead], (int)d->c, w);
+        else fill_axis(&P.ax[a], d->axis[a - lead], d->in_shape[a - lead], (int)d->c, w, d->align, keys_a(d));
     }
     P.planes = d->n * d->c;
     P.C = (int)d->c;

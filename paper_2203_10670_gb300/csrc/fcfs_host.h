@@ -19,7 +19,8 @@ int fail(int status, const char* fmt, ...);
 void clear_error();
 int cuda_fail(cudaError_t e, const char* what);
 
-double kernel_value(int method, double t);
+double kernel_value(int method, double t, double ka);
+double keys_a(const fcfs_desc* d);
 int support_radius(int method);
 int k_min(int method, int s);
 long long out_len(long long n, int r, int s);
@@ -32,7 +33,7 @@ long long numel_in(const fcfs_desc* d);
 long long numel_out(const fcfs_desc* d);
 int dtype_size(int dt);
 
-void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel);
+void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel, int align, double ka);
 void identity_axis(AxisP* A, int nt_kernel);
 
 int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* out, int* ntk);

@@ -202,6 +202,7 @@ struct NearestParams {
     int r[3], s[3], n_in[3], n_out[3];
     long long planes;
     int pad;
+    int align;  // fcfs_align: source index rule
     float padv;
     int OXT, OYT;  // outputs per block along x and y
     int tiles_x, tiles_y;

@@ -18,11 +18,13 @@ import numpy as np
 import torch
 
 from . import _native as N
-from ._native import (FCFS_BF16, FCFS_BICUBIC, FCFS_BILINEAR, FCFS_F32, FCFS_NEAREST, FCFS_PAD_CONSTANT,
-                      FCFS_PAD_REFLECT, FCFS_PAD_REPLICATE, FCFS_U8, FCFSError, check)
+from ._native import (FCFS_ALIGN_FLOOR, FCFS_ALIGN_HALF_PIXEL, FCFS_ALIGN_PAPER, FCFS_BF16, FCFS_BICUBIC,
+                      FCFS_BILINEAR, FCFS_F32, FCFS_NEAREST, FCFS_PAD_CONSTANT, FCFS_PAD_REFLECT, FCFS_PAD_REPLICATE,
+                      FCFS_U8, FCFSError, check)
 
 NEAREST, BILINEAR, BICUBIC = FCFS_NEAREST, FCFS_BILINEAR, FCFS_BICUBIC
 PAD_REPLICATE, PAD_CONSTANT, PAD_REFLECT = FCFS_PAD_REPLICATE, FCFS_PAD_CONSTANT, FCFS_PAD_REFLECT
+ALIGN_PAPER, ALIGN_HALF_PIXEL, ALIGN_FLOOR = FCFS_ALIGN_PAPER, FCFS_ALIGN_HALF_PIXEL, FCFS_ALIGN_FLOOR
 
 _DT = {torch.float32: FCFS_F32, torch.bfloat16: FCFS_BF16, torch.uint8: FCFS_U8}
 _TD = {FCFS_F32: torch.float32, FCFS_BF16: torch.bfloat16, FCFS_U8: torch.uint8}
@@ -114,8 +116,11 @@ def out_len(n: int, r: int, s: int) -> int:
 
 
 def make_desc(shape: Sequence[int], axes: Sequence[Axis], dtype_in: int, dtype_out: int,
-              pad: int = PAD_REPLICATE, pad_value: float = 0.0) -> N.fcfs_desc:
-    """Descriptor for an input of shape [n, c, *spatial] (spatial outermost first)."""
+              pad: int = PAD_REPLICATE, pad_value: float = 0.0, align: int = ALIGN_PAPER,
+              cubic_a: float = 0.0) -> N.fcfs_desc:
+    """Descriptor for an input of shape [n, c, *spatial] (spatial outermost first).
+    align / cubic_a: sample alignment and Keys parameter of the fixed methods
+    (ALIGN_PAPER and 0 = the paper's -0.5 by default)."""
     nd = len(shape) - 2
     if nd != len(axes) or not 1 <= nd <= 3:
         raise ValueError(f"{len(axes)} axes for a tensor with {nd} spatial dims")
@@ -144,7 +149,8 @@ def make_desc(shape: Sequence[int], axes: Sequence[Axis], dtype_in: int, dtype_o
             d.axis[a].w_per_channel = 0
     d.dtype_in, d.dtype_out = dtype_in, dtype_out
     d.pad, d.pad_value = pad, float(pad_value)
-    d.align = 0
+    d.align = int(align)
+    d.cubic_a = float(cubic_a)
     return d
 
 
@@ -159,7 +165,8 @@ def _stream(device) -> int:
 # ------------------------------------------------------------ tensor level
 
 def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_value: float = 0.0,
-           out_dtype: Optional[torch.dtype] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+           out_dtype: Optional[torch.dtype] = None, out: Optional[torch.Tensor] = None, align: int = ALIGN_PAPER,
+           cubic_a: float = 0.0) -> torch.Tensor:
     """y = FCFS(x) for x [n, c, *spatial] (float32, bfloat16 or uint8).
 
     A CUDA tensor is processed on its device and current stream.  A host tensor
@@ -167,7 +174,7 @@ def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_
     back to host memory (pinned inputs make both copies asynchronous)."""
     if not x.is_cuda:
         dev = torch.device("cuda", torch.cuda.current_device())
-        y = resize(x.to(dev, non_blocking=True), axes, pad, pad_value, out_dtype)
+        y = resize(x.to(dev, non_blocking=True), axes, pad, pad_value, out_dtype, align=align, cubic_a=cubic_a)
         if out is not None:
             out.copy_(y)
             return out
@@ -175,7 +182,7 @@ def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_
     if out_dtype is None:
         out_dtype = torch.float32 if x.dtype == torch.uint8 else x.dtype
     x = x.contiguous()
-    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value)
+    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value, align, cubic_a)
     oshape = out_shape(x.shape, axes)
     if out is None:
         out = torch.empty(oshape, dtype=out_dtype, device=x.device)
@@ -187,14 +194,14 @@ def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_
 
 def resize_backward(x: Optional[torch.Tensor], gy: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE,
                     pad_value: float = 0.0, in_shape=None, in_dtype=None, need_dx: bool = True,
-                    need_dw: Sequence[bool] = ()):
+                    need_dw: Sequence[bool] = (), align: int = ALIGN_PAPER, cubic_a: float = 0.0):
     """(gx, [gw per axis]) of the FCFS forward for upstream gradient gy."""
     if in_shape is None:
         in_shape = tuple(x.shape)
     if in_dtype is None:
         in_dtype = x.dtype
     gy = gy.contiguous()
-    d = make_desc(in_shape, axes, _DT[in_dtype], _DT[gy.dtype], pad, pad_value)
+    d = make_desc(in_shape, axes, _DT[in_dtype], _DT[gy.dtype], pad, pad_value, align, cubic_a)
     dev = gy.device
     gx = torch.empty(in_shape, dtype=in_dtype, device=dev) if need_dx else None
     gws, ptrs = [], []
@@ -220,7 +227,8 @@ class FCFSFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, spec, *weights):
         axes = [Axis(a.r, a.s, a.method, a.K, w) for a, w in zip(spec["axes"], weights)]
-        y = resize(x, axes, spec["pad"], spec["pad_value"], spec.get("out_dtype"))
+        y = resize(x, axes, spec["pad"], spec["pad_value"], spec.get("out_dtype"), align=spec.get("align", ALIGN_PAPER),
+                   cubic_a=spec.get("cubic_a", 0.0))
         ctx.spec = spec
         ctx.save_for_backward(x, *[w if w is not None else torch.empty(0) for w in weights])
         ctx.has_w = [w is not None for w in weights]
@@ -234,7 +242,8 @@ class FCFSFunction(torch.autograd.Function):
         need_w = [h and ctx.needs_input_grad[2 + i] for i, h in enumerate(ctx.has_w)]
         gx, gws = resize_backward(x if any(need_w) else None, gy.to(spec.get("out_dtype") or x.dtype), axes,
                                   spec["pad"], spec["pad_value"], in_shape=tuple(x.shape), in_dtype=x.dtype,
-                                  need_dx=ctx.needs_input_grad[0], need_dw=need_w)
+                                  need_dx=ctx.needs_input_grad[0], need_dw=need_w,
+                                  align=spec.get("align", ALIGN_PAPER), cubic_a=spec.get("cubic_a", 0.0))
         return (gx, None, *gws)
 
 
@@ -245,10 +254,12 @@ class FCFS(torch.nn.Module):
     per-channel taps [C, r, 2K+1] initialised to the method's table."""
 
     def __init__(self, channels: int, ratios, method: int = BILINEAR, pad: int = PAD_REPLICATE,
-                 pad_value: float = 0.0, learnable: bool = False, K: int = 0, out_dtype=None):
+                 pad_value: float = 0.0, learnable: bool = False, K: int = 0, out_dtype=None,
+                 align: int = ALIGN_PAPER, cubic_a: float = 0.0):
         super().__init__()
         self.ratios = [tuple(rs) for rs in ratios]
         self.method, self.pad, self.pad_value, self.out_dtype = method, pad, pad_value, out_dtype
+        self.align, self.cubic_a = align, cubic_a  # fixed-method sampling (learnable taps ignore it)
         self.weights = torch.nn.ParameterList()
         self.Ks = []
         for r, s in self.ratios:
@@ -260,7 +271,8 @@ class FCFS(torch.nn.Module):
 
     def forward(self, x):
         spec = {"axes": [Axis(r, s, self.method, k) for (r, s), k in zip(self.ratios, self.Ks)],
-                "pad": self.pad, "pad_value": self.pad_value, "out_dtype": self.out_dtype}
+                "pad": self.pad, "pad_value": self.pad_value, "out_dtype": self.out_dtype,
+                "align": self.align, "cubic_a": self.cubic_a}
         ws = [w.contiguous() for w in self.weights] if self.learnable else [None] * len(self.ratios)
         return FCFSFunction.apply(x, spec, *ws)
 
@@ -306,11 +318,12 @@ class Server:
         return N.load().fcfs_serve_clock()
 
     def submit(self, x: torch.Tensor, ratio, method: int = BILINEAR, y: Optional[torch.Tensor] = None,
-               arrival: Optional[float] = None, pad: int = PAD_REPLICATE, pad_value: float = 0.0) -> int:
+               arrival: Optional[float] = None, pad: int = PAD_REPLICATE, pad_value: float = 0.0,
+               align: int = ALIGN_PAPER, cubic_a: float = 0.0) -> int:
         r, s = ratio
         axes = [Axis(r, s, method)] * 2
         dout = _DT[y.dtype] if y is not None else _DT[self.out_dtype]
-        d = make_desc(x.shape, axes, _DT[x.dtype], dout, pad, pad_value)
+        d = make_desc(x.shape, axes, _DT[x.dtype], dout, pad, pad_value, align, cubic_a)
         rid = ctypes.c_ulonglong()
         t = self.clock() if arrival is None else float(arrival)
         check(self._lib.fcfs_serve_submit(self._h, ctypes.byref(d), x.data_ptr(),

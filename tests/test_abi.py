@@ -106,7 +106,8 @@ BOGUS = 0x1000  # never dereferenced: every case fails validation first
 
 @pytest.mark.parametrize("field,value,status", [
     ("ndim", 0, -1), ("ndim", 4, -1), ("n", -1, -1), ("dtype_in", 7, -1), ("dtype_out", 2, -1),
-    ("pad", 3, -1), ("align", 1, -3),
+    ("pad", 3, -1), ("align", 3, -1), ("align", -1, -1), ("cubic_a", float("inf"), -1),
+    ("cubic_a", float("nan"), -1),
 ])
 def test_forward_rejects_bad_descriptor(native, field, value, status):
     lib = native.load()
