@@ -75,6 +75,9 @@ def lib():
         L.orc_adjoint_dx.argtypes = [i, ll, ll, P, P, i, P, P]
         L.orc_adjoint_dx_at.argtypes = [i, ll, ll, P, P, i, P, P, ll, P]
         L.orc_weight_grad.argtypes = [i, ll, ll, P, P, i, d, P, P, P]
+        L.orc_resize_full2d.argtypes = [ll, ll, P, P, P, i, i, d, P, P]
+        L.orc_adjoint_full2d.argtypes = [ll, ll, P, P, P, i, i, P, P]
+        L.orc_weight_grad_full2d.argtypes = [ll, ll, P, P, i, i, d, P, P, P]
         _lib = L
     return _lib
 
@@ -244,3 +247,60 @@ def weight_grad(x, g, axes, pad=PAD_REPLICATE, pad_value=0.0):
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return outs
+
+
+# ------------------------------------------------ non-separable 2D kernels
+
+def _full_axes(axes):
+    keep = []
+    ax = _axes([dict(r=a["r"], s=a["s"], method=a.get("method", BILINEAR), K=a.get("K", 0)) for a in axes], keep)
+    return ax
+
+
+def resize_full2d(x, axes, w, pad=PAD_REPLICATE, pad_value=0.0):
+    """Non-separable 2D FCFS: w [C][r_y][r_x][T_y][T_x] (per channel) or [r_y][r_x][T_y][T_x];
+    axes: two dicts {r, s, K (or method for K_min)}."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n, c, spatial = x.shape[0], x.shape[1], x.shape[2:]
+    assert len(spatial) == 2 and len(axes) == 2
+    ax = _full_axes(axes)
+    y = np.empty((n, c) + out_shape(spatial, axes), dtype=np.float64)
+    if y.size == 0:
+        return y
+    rc = lib().orc_resize_full2d(n, c, _shapes(spatial), ctypes.cast(ax, ctypes.c_void_p), w.ctypes.data,
+                                 1 if w.ndim == 5 else 0, pad, float(pad_value), x.ctypes.data, y.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return y
+
+
+def adjoint_full2d(g, in_shape, axes, w, pad=PAD_REPLICATE):
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n, c = g.shape[0], g.shape[1]
+    ax = _full_axes(axes)
+    dx = np.zeros((n, c) + tuple(in_shape), dtype=np.float64)
+    if dx.size == 0:
+        return dx
+    rc = lib().orc_adjoint_full2d(n, c, _shapes(in_shape), ctypes.cast(ax, ctypes.c_void_p), w.ctypes.data,
+                                  1 if w.ndim == 5 else 0, pad, g.ctypes.data, dx.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return dx
+
+
+def weight_grad_full2d(x, g, axes, per_channel, pad=PAD_REPLICATE, pad_value=0.0):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n, c, spatial = x.shape[0], x.shape[1], x.shape[2:]
+    ax = _full_axes(axes)
+    T = [2 * ax[k].K + 1 for k in range(2)]
+    shape = (axes[0]["r"], axes[1]["r"], T[0], T[1])
+    dw = np.zeros(((c,) + shape) if per_channel else shape, dtype=np.float64)
+    rc = lib().orc_weight_grad_full2d(n, c, _shapes(spatial), ctypes.cast(ax, ctypes.c_void_p),
+                                      1 if per_channel else 0, pad, float(pad_value), x.ctypes.data, g.ctypes.data,
+                                      dw.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return dw

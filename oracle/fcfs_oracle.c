@@ -567,3 +567,142 @@ int orc_weight_grad(int ndim, long long n, long long c, const long long* in_shap
     free_tables(tables);
     return 0;
 }
+
+/* ------------------------------------------------- non-separable 2D kernels */
+
+/* Full (non-separable) 2D kernels, the ND convolution of Sec. 4 with one
+ * learnable T_y x T_x kernel per phase pair instead of an outer product:
+ *   y[n,c, iy r_y + jy, ix r_x + jx] = sum_{my, mx} W[c][jy][jx][my][mx]
+ *                                      x~[n,c, iy s_y - L_y + my, ix s_x - L_x + mx]
+ * W is [C][r_y][r_x][T_y][T_x] (per_channel) or [r_y][r_x][T_y][T_x];
+ * T_a = 2 K_a + 1, L_a = K_a - floor(s_a / 2), K_a from the axis (0 -> K_min of
+ * its method).  x~ is the padded input (constant pad samples carry pad_value). */
+typedef struct {
+    long long n_in, n_out;
+    int r, s, K, T, L;
+} full_axis_t;
+
+static int full_axes(const long long* in_shape, const orc_axis* axes, full_axis_t f[2]) {
+    for (int a = 0; a < 2; ++a) {
+        const orc_axis* g = &axes[a];
+        if (g->r < 1 || g->s < 1) return -1;
+        f[a].n_in = in_shape[a];
+        f[a].r = g->r;
+        f[a].s = g->s;
+        f[a].K = g->K ? g->K : orc_kmin(g->method, g->s);
+        f[a].T = 2 * f[a].K + 1;
+        f[a].L = orc_left_offset(f[a].K, f[a].s);
+        f[a].n_out = orc_out_len(f[a].n_in, f[a].r, f[a].s);
+    }
+    return 0;
+}
+
+static double full_weight(const full_axis_t f[2], const double* w, int per_channel, long long ch, int jy, int jx,
+                          int my, int mx) {
+    long long per = (long long)f[0].r * f[1].r * f[0].T * f[1].T;
+    return w[(per_channel ? ch * per : 0) + (((long long)jy * f[1].r + jx) * f[0].T + my) * f[1].T + mx];
+}
+
+int orc_resize_full2d(long long n, long long c, const long long* in_shape, const orc_axis* axes, const double* w,
+                      int per_channel, int pad, double pad_value, const double* x, double* y) {
+    full_axis_t f[2];
+    if (full_axes(in_shape, axes, f) != 0) return -1;
+    long long in_plane = f[0].n_in * f[1].n_in, out_plane = f[0].n_out * f[1].n_out;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long p = 0; p < n * c; ++p) {
+        long long ch = p % c;
+        const double* plane = x + p * in_plane;
+        for (long long oy = 0; oy < f[0].n_out; ++oy)
+            for (long long ox = 0; ox < f[1].n_out; ++ox) {
+                long long iy = oy / f[0].r, ix = ox / f[1].r;
+                int jy = (int)(oy % f[0].r), jx = (int)(ox % f[1].r);
+                double acc = 0.0;
+                for (int my = 0; my < f[0].T; ++my) {
+                    long long qy = orc_ext_index(iy * f[0].s - f[0].L + my, f[0].n_in, pad);
+                    for (int mx = 0; mx < f[1].T; ++mx) {
+                        long long qx = orc_ext_index(ix * f[1].s - f[1].L + mx, f[1].n_in, pad);
+                        double v = (qy < 0 || qx < 0) ? pad_value : plane[qy * f[1].n_in + qx];
+                        acc += full_weight(f, w, per_channel, ch, jy, jx, my, mx) * v;
+                    }
+                }
+                y[p * out_plane + oy * f[1].n_out + ox] = acc;
+            }
+    }
+    return 0;
+}
+
+/* Input gradient: the transposed sum, every output sending W * g to the real
+ * pixel its extended tap maps to (replicate / reflect fold, constant drops). */
+int orc_adjoint_full2d(long long n, long long c, const long long* in_shape, const orc_axis* axes, const double* w,
+                       int per_channel, int pad, const double* g, double* dx) {
+    full_axis_t f[2];
+    if (full_axes(in_shape, axes, f) != 0) return -1;
+    long long in_plane = f[0].n_in * f[1].n_in, out_plane = f[0].n_out * f[1].n_out;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long p = 0; p < n * c; ++p) {
+        long long ch = p % c;
+        double* d = dx + p * in_plane;
+        for (long long k = 0; k < in_plane; ++k) d[k] = 0.0;
+        for (long long oy = 0; oy < f[0].n_out; ++oy)
+            for (long long ox = 0; ox < f[1].n_out; ++ox) {
+                long long iy = oy / f[0].r, ix = ox / f[1].r;
+                int jy = (int)(oy % f[0].r), jx = (int)(ox % f[1].r);
+                double gv = g[p * out_plane + oy * f[1].n_out + ox];
+                for (int my = 0; my < f[0].T; ++my) {
+                    long long qy = orc_ext_index(iy * f[0].s - f[0].L + my, f[0].n_in, pad);
+                    if (qy < 0) continue;
+                    for (int mx = 0; mx < f[1].T; ++mx) {
+                        long long qx = orc_ext_index(ix * f[1].s - f[1].L + mx, f[1].n_in, pad);
+                        if (qx < 0) continue;
+                        d[qy * f[1].n_in + qx] += full_weight(f, w, per_channel, ch, jy, jx, my, mx) * gv;
+                    }
+                }
+            }
+    }
+    return 0;
+}
+
+/* Weight gradient: dW[c][jy][jx][my][mx] = sum over n and windows of
+ * g[iy r_y + jy][ix r_x + jx] x~[iy s_y - L_y + my][ix s_x - L_x + mx]
+ * (summed over channels, in channel order, when the kernel is shared). */
+int orc_weight_grad_full2d(long long n, long long c, const long long* in_shape, const orc_axis* axes, int per_channel,
+                           int pad, double pad_value, const double* x, const double* g, double* dw) {
+    full_axis_t f[2];
+    if (full_axes(in_shape, axes, f) != 0) return -1;
+    long long in_plane = f[0].n_in * f[1].n_in, out_plane = f[0].n_out * f[1].n_out;
+    long long per = (long long)f[0].r * f[1].r * f[0].T * f[1].T;
+    double* part = (double*)calloc((size_t)(c * per), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long ch = 0; ch < c; ++ch) {
+        double* P = part + ch * per;
+        for (long long b = 0; b < n; ++b) {
+            long long p = b * c + ch;
+            const double* plane = x + p * in_plane;
+            for (long long oy = 0; oy < f[0].n_out; ++oy)
+                for (long long ox = 0; ox < f[1].n_out; ++ox) {
+                    long long iy = oy / f[0].r, ix = ox / f[1].r;
+                    int jy = (int)(oy % f[0].r), jx = (int)(ox % f[1].r);
+                    double gv = g[p * out_plane + oy * f[1].n_out + ox];
+                    for (int my = 0; my < f[0].T; ++my) {
+                        long long qy = orc_ext_index(iy * f[0].s - f[0].L + my, f[0].n_in, pad);
+                        for (int mx = 0; mx < f[1].T; ++mx) {
+                            long long qx = orc_ext_index(ix * f[1].s - f[1].L + mx, f[1].n_in, pad);
+                            double v = (qy < 0 || qx < 0) ? pad_value : plane[qy * f[1].n_in + qx];
+                            P[(((long long)jy * f[1].r + jx) * f[0].T + my) * f[1].T + mx] += gv * v;
+                        }
+                    }
+                }
+        }
+    }
+    if (per_channel) {
+        memcpy(dw, part, sizeof(double) * (size_t)(c * per));
+    } else {
+        for (long long e = 0; e < per; ++e) {
+            double s = 0.0;
+            for (long long ch = 0; ch < c; ++ch) s += part[ch * per + e];
+            dw[e] = s;
+        }
+    }
+    free(part);
+    return 0;
+}

@@ -678,3 +678,92 @@ def test_variant_adjoint_dot_product(orc, pad, axes):
     dx = orc.adjoint_dx(g, (9, 11), axes, pad=pad)
     lhs, rhs = np.vdot(y, g), np.vdot(x, dx)
     assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.abs(y).sum())
+
+
+# -------------------------------------------- non-separable 2D kernels (f2)
+# One learnable T_y x T_x kernel per phase pair (Sec. 4's ND convolution without
+# the outer-product restriction).  Pinned to the paper's construction built from
+# PyTorch CPU library ops in float64 (pad -> grouped strided conv2d -> pixel
+# shuffle -> crop), whose autograd also pins the input and weight gradients.
+
+def _full2d_construction(x, w, ratios, Ks, pad, pad_value):
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    n, c, H, W = x.shape
+    (ry, sy), (rx, sx) = ratios
+    Ty, Tx = 2 * Ks[0] + 1, 2 * Ks[1] + 1
+    Ly, Lx = Ks[0] - sy // 2, Ks[1] - sx // 2
+    Ho, Wo = H * ry // sy, W * rx // sx
+    nwy, nwx = -(-Ho // ry), -(-Wo // rx)
+    ry_pad = max(0, (nwy - 1) * sy - Ly + Ty - H)
+    rx_pad = max(0, (nwx - 1) * sx - Lx + Tx - W)
+    xt = x if isinstance(x, torch.Tensor) else torch.from_numpy(x)
+    mode = {REPL: "replicate", CONST: "constant", REFL: "reflect"}[pad]
+    kw = {"value": pad_value} if pad == CONST else {}
+    # left pads may be negative (a window that starts inside the image): crop instead
+    xp = F.pad(xt, (max(Lx, 0), rx_pad, max(Ly, 0), ry_pad), mode=mode, **kw)
+    xp = xp[:, :, max(-Ly, 0):, max(-Lx, 0):]
+    wt = w if isinstance(w, torch.Tensor) else torch.from_numpy(w)
+    if wt.dim() == 4:
+        wt = wt.unsqueeze(0).expand(c, *wt.shape)
+    k = wt.reshape(c * ry * rx, 1, Ty, Tx)
+    z = F.conv2d(xp, k, stride=(sy, sx), groups=c)[:, :, :nwy, :nwx]
+    z = z.reshape(n, c, ry, rx, nwy, nwx).permute(0, 1, 4, 2, 5, 3).reshape(n, c, nwy * ry, nwx * rx)
+    return z[:, :, :Ho, :Wo]
+
+
+FULL_CASES = [(((3, 2), (2, 3)), (1, 2)), (((5, 4), (5, 4)), (2, 2)), (((2, 1), (3, 2)), (1, 1)), (((4, 3), (1, 2)), (2, 1))]
+
+
+@pytest.mark.parametrize("ratios,Ks", FULL_CASES)
+@pytest.mark.parametrize("pad", (REPL, CONST, REFL))
+@pytest.mark.parametrize("per_channel", (True, False))
+def test_full2d_matches_construction(orc, ratios, Ks, pad, per_channel):
+    rng = np.random.default_rng(51)
+    C = 3
+    (ry, _), (rx, _) = ratios
+    shape = (ry, rx, 2 * Ks[0] + 1, 2 * Ks[1] + 1)
+    w = rng.standard_normal(((C,) + shape) if per_channel else shape)
+    x = rng.standard_normal((2, C, 11, 13))
+    axes = [dict(r=r, s=s, K=K) for (r, s), K in zip(ratios, Ks)]
+    got = orc.resize_full2d(x, axes, w, pad=pad, pad_value=0.4)
+    want = _full2d_construction(x, w, ratios, Ks, pad, 0.4).numpy()
+    assert got.shape == want.shape
+    assert np.abs(got - want).max() <= 1e-12 * (1 + np.abs(want).max())
+
+
+@pytest.mark.parametrize("ratios,Ks", FULL_CASES[:2])
+@pytest.mark.parametrize("pad", (REPL, CONST, REFL))
+def test_full2d_gradients_match_construction_autograd(orc, ratios, Ks, pad):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(52)
+    C = 2
+    (ry, _), (rx, _) = ratios
+    w = torch.tensor(rng.standard_normal((C, ry, rx, 2 * Ks[0] + 1, 2 * Ks[1] + 1)), requires_grad=True)
+    x = torch.tensor(rng.standard_normal((2, C, 10, 12)), requires_grad=True)
+    y = _full2d_construction(x, w, ratios, Ks, pad, 0.0)
+    g = torch.tensor(rng.standard_normal(tuple(y.shape)))
+    (y * g).sum().backward()
+    axes = [dict(r=r, s=s, K=K) for (r, s), K in zip(ratios, Ks)]
+    dx = orc.adjoint_full2d(g.numpy(), (10, 12), axes, w.detach().numpy(), pad=pad)
+    dw = orc.weight_grad_full2d(x.detach().numpy(), g.numpy(), axes, True, pad=pad)
+    assert np.abs(dx - x.grad.numpy()).max() <= 1e-12 * (1 + np.abs(dx).max())
+    assert np.abs(dw - w.grad.numpy()).max() <= 1e-12 * (1 + np.abs(dw).max())
+
+
+def test_full2d_outer_product_is_the_separable_layer(orc):
+    rng = np.random.default_rng(53)
+    C = 2
+    wy = rng.standard_normal((C, 3, 5))
+    wx = rng.standard_normal((C, 2, 3))
+    w = np.einsum("cjm,ckn->cjkmn", wy, wx)
+    x = rng.standard_normal((1, C, 12, 14))
+    sep = orc.resize(x, [dict(r=3, s=2, K=2, w=wy), dict(r=2, s=3, K=1, w=wx)], pad=REFL, polyphase=True)
+    full = orc.resize_full2d(x, [dict(r=3, s=2, K=2), dict(r=2, s=3, K=1)], w, pad=REFL)
+    assert np.abs(sep - full).max() <= 1e-13 * (1 + np.abs(sep).max())
+    # shared kernels sum the channels' weight gradients
+    g = rng.standard_normal(full.shape)
+    axes = [dict(r=3, s=2, K=2), dict(r=2, s=3, K=1)]
+    per = orc.weight_grad_full2d(x, g, axes, True, pad=REFL)
+    shared = orc.weight_grad_full2d(x, g, axes, False, pad=REFL)
+    assert np.abs(per.sum(0) - shared).max() <= 1e-12 * (1 + np.abs(shared).max())
