@@ -122,7 +122,24 @@ typedef struct {
     fcfs_axis axis[3];       /* same order as in_shape */
     float cubic_a;           /* Keys parameter of the fixed bicubic: 0 selects the
                                 paper's -0.5 (Sec. 5.2); -0.75 is another common choice */
+    const float* w2d;        /* DEVICE non-separable 2D kernels, NULL for the separable
+                                layer; see "Non-separable 2D kernels" below */
+    int w2d_per_channel;     /* 1: w2d is [C][r_y][r_x][T_y][T_x], 0: [r_y][r_x][T_y][T_x] */
 } fcfs_desc;
+
+/*
+ * Non-separable 2D kernels (w2d != NULL): the 2D convolution of Sec. 4 with a
+ * general T_y x T_x kernel per phase pair instead of the outer product of the
+ * two axis kernels, so that learning can change the kernel's shape (Sec. 6):
+ *   y[n,c, iy r_y + jy, ix r_x + jx] = sum_{my,mx} w2d[c][jy][jx][my][mx]
+ *                                      x~[n,c, iy s_y - L_y + my, ix s_x - L_x + mx]
+ * Requires ndim == 2 and axis[a].w == NULL; axis[a] gives r, s and K (0 = K_min
+ * of axis[a].method), T_a = 2 K_a + 1 <= FCFS_MAX_TAPS, L_a = K_a - floor(s_a/2),
+ * and r_y r_x T_y T_x <= 4096.  align and cubic_a do not apply.  fcfs_forward
+ * and fcfs_backward take such descriptors (fcfs_backward writes the gradient
+ * of w2d, shaped like w2d, to gw[0] and needs gw[1] == NULL); the serving API
+ * and fcfs_tune_forward reject them with FCFS_ERR_UNSUPPORTED.
+ */
 
 /*
  * Forward FCFS (Sec. 3.2 pseudocode; Sec. 4 for 2D/3D):

@@ -130,8 +130,20 @@ int validate_desc(const fcfs_desc* d, bool output_dtype_check) {
     if (d->align < FCFS_ALIGN_PAPER || d->align > FCFS_ALIGN_FLOOR) return fail(FCFS_ERR_ARG, "unknown alignment %d", d->align);
     if (!std::isfinite(d->cubic_a)) return fail(FCFS_ERR_ARG, "cubic_a must be finite");
     if (d->c > INT_MAX) return fail(FCFS_ERR_ARG, "c too large");
+    if (d->w2d) {
+        if (d->ndim != 2) return fail(FCFS_ERR_ARG, "non-separable kernels (w2d) need ndim == 2 (got %d)", d->ndim);
+        if (d->w2d_per_channel != 0 && d->w2d_per_channel != 1)
+            return fail(FCFS_ERR_ARG, "w2d_per_channel must be 0 or 1");
+    }
     for (int a = 0; a < d->ndim; ++a) {
-        int rc = validate_axis(d->axis[a], a);
+        fcfs_axis ax = d->axis[a];
+        if (d->w2d) {
+            // the axis gives r, s and K of the non-separable kernel, checked like learnable weights
+            if (ax.w) return fail(FCFS_ERR_ARG, "axis %d: per-axis weights and w2d are exclusive", a);
+            ax.w = d->w2d;
+            ax.w_per_channel = d->w2d_per_channel;
+        }
+        int rc = validate_axis(ax, a);
         if (rc) return rc;
         if (d->in_shape[a] < 0 || d->in_shape[a] > INT_MAX / 2)
             return fail(FCFS_ERR_ARG, "axis %d: input extent %lld out of range", a, d->in_shape[a]);
@@ -394,6 +406,7 @@ int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
     if (((uintptr_t)x) % dtype_size(d->dtype_in) || ((uintptr_t)y) % dtype_size(d->dtype_out))
         return fail(FCFS_ERR_ARG, "x or y not aligned to its element size");
     cudaStream_t st = (cudaStream_t)stream;
+    if (d->w2d) return full2d_forward(d, x, y, st);
 
     bool all_nearest = true;
     for (int a = 0; a < d->ndim; ++a) all_nearest &= (d->axis[a].w == nullptr && d->axis[a].method == FCFS_NEAREST);
@@ -1003,6 +1016,39 @@ static size_t dw_workspace(const BwdParams& B) {
     return (size_t)(((recs * B.dw_rec * sizeof(float)) + 255) / 256 * 256);
 }
 
+// Backward of the non-separable 2D layer: gw[0] (if given) receives the
+// gradient of w2d, gw[1] must be NULL.
+static int backward_full2d(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw, void* ws,
+                           size_t ws_bytes, cudaStream_t st) {
+    float* gw2d = gw ? gw[0] : nullptr;
+    if (gw && gw[1]) return fail(FCFS_ERR_ARG, "gw[1] must be NULL with w2d (gw[0] receives its gradient)");
+    if (gw2d && ((uintptr_t)gw2d) % 4) return fail(FCFS_ERR_ARG, "gw[0] not 4-byte aligned");
+    if (!gx && !gw2d) return FCFS_OK;
+    if (numel_in(d) == 0) return FCFS_OK;
+    if (gy && ((uintptr_t)gy) % dtype_size(d->dtype_out)) return fail(FCFS_ERR_ARG, "gy misaligned");
+    if (gx && ((uintptr_t)gx) % dtype_size(d->dtype_in)) return fail(FCFS_ERR_ARG, "gx misaligned");
+    if (numel_out(d) == 0) {
+        if (gx) {
+            cudaError_t e = cudaMemsetAsync(gx, 0, (size_t)numel_in(d) * dtype_size(d->dtype_in), st);
+            if (e != cudaSuccess) return cuda_fail(e, "memset gx");
+        }
+        if (gw2d) {
+            size_t n = (size_t)(d->w2d_per_channel ? d->c : 1) * d->axis[0].r * d->axis[1].r;
+            for (int a = 0; a < 2; ++a) n *= 2 * (d->axis[a].K ? d->axis[a].K : k_min(d->axis[a].method, d->axis[a].s)) + 1;
+            cudaError_t e = cudaMemsetAsync(gw2d, 0, n * sizeof(float), st);
+            if (e != cudaSuccess) return cuda_fail(e, "memset gw");
+        }
+        return FCFS_OK;
+    }
+    if (!gy) return fail(FCFS_ERR_ARG, "gy is NULL");
+    if (gw2d) {
+        if (!x) return fail(FCFS_ERR_ARG, "x is required for weight gradients");
+        if (((uintptr_t)x) % dtype_size(d->dtype_in)) return fail(FCFS_ERR_ARG, "x misaligned");
+        if (((uintptr_t)ws) % 256) return fail(FCFS_ERR_ARG, "workspace not 256-byte aligned");
+    }
+    return full2d_backward(d, x, gy, gx, gw2d, ws, ws_bytes, st);
+}
+
 static bool any_learnable(const fcfs_desc* d) {
     for (int a = 0; a < d->ndim; ++a)
         if (d->axis[a].w) return true;
@@ -1016,6 +1062,7 @@ extern "C" {
 size_t fcfs_backward_workspace(const fcfs_desc* d) {
     clear_error();
     if (validate_desc(d, true) != FCFS_OK) return 0;
+    if (d->w2d) return numel_out(d) == 0 ? 0 : full2d_workspace(d);
     if (!any_learnable(d) || d->ndim == 3 || numel_out(d) == 0) return 0;
     BwdParams B;
     int ntk;
@@ -1035,6 +1082,7 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
     if (rc) return rc;
     if (d->dtype_in == FCFS_U8) return fail(FCFS_ERR_UNSUPPORTED, "no gradient for uint8 inputs");
     bool want_w = false;
+    if (d->w2d) return backward_full2d(d, x, gy, gx, gw, workspace, ws_bytes, (cudaStream_t)stream);
     for (int a = 0; a < d->ndim && gw; ++a) {
         if (!gw[a]) continue;
         if (!d->axis[a].w) return fail(FCFS_ERR_ARG, "gw[%d] given but axis %d has no learnable weights", a, a);

@@ -51,4 +51,10 @@ bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t);
 int launch_planned(FwdParams& P, int ntk, bool is3d, int din, int dout, cudaStream_t st);
 int build_adjoint(const AxisP& A, AdjAxis* J);
 
+// non-separable 2D kernels (fcfs_full2d.cu)
+int full2d_forward(const fcfs_desc* d, const void* x, void* y, cudaStream_t st);
+size_t full2d_workspace(const fcfs_desc* d);
+int full2d_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* gw, void* ws,
+                    size_t ws_bytes, cudaStream_t st);
+
 }  // namespace fcfs

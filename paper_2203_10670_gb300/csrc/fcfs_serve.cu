@@ -268,6 +268,7 @@ int fcfs_serve_submit(void* h, const fcfs_desc* d, const void* x, void* y, doubl
     int rc = validate_desc(d, true);
     if (rc) return rc;
     if (d->ndim != 2) return fail(FCFS_ERR_UNSUPPORTED, "serving takes 2D images");
+    if (d->w2d) return fail(FCFS_ERR_UNSUPPORTED, "serving uses separable kernels");
     for (int a = 0; a < 2; ++a)
         if (d->axis[a].w) return fail(FCFS_ERR_UNSUPPORTED, "serving uses the fixed method tables");
     if (!x) return fail(FCFS_ERR_ARG, "x is NULL");

@@ -13,6 +13,7 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     clear_error();
     int rc = validate_desc(d, true);
     if (rc) return rc;
+    if (d->w2d) return fail(FCFS_ERR_UNSUPPORTED, "the tile search covers the separable kernels");
     if (reps < 1) reps = 3;
     if (best_ms) *best_ms = 0.f;
     if (n_candidates) *n_candidates = 0;

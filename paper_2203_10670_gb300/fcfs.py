@@ -277,6 +277,106 @@ class FCFS(torch.nn.Module):
         return FCFSFunction.apply(x, spec, *ws)
 
 
+# ------------------------------------------------- non-separable 2D kernels
+
+def _full2d_axes(axes: Sequence[Axis], w2d: torch.Tensor):
+    if len(axes) != 2:
+        raise ValueError("non-separable kernels take two spatial axes")
+    if w2d.dtype != torch.float32 or not w2d.is_cuda or not w2d.is_contiguous() or w2d.dim() not in (4, 5):
+        raise ValueError("w2d must be a contiguous float32 CUDA tensor [C, r_y, r_x, T_y, T_x] or [r_y, r_x, T_y, T_x]")
+    ry, rx, Ty, Tx = w2d.shape[-4:]
+    if (ry, rx) != (axes[0].r, axes[1].r) or Ty % 2 == 0 or Tx % 2 == 0:
+        raise ValueError("w2d must have r_y x r_x phases of odd T_y x T_x taps")
+    return [Axis(axes[0].r, axes[0].s, axes[0].method, (Ty - 1) // 2),
+            Axis(axes[1].r, axes[1].s, axes[1].method, (Tx - 1) // 2)]
+
+
+def make_desc_full2d(shape: Sequence[int], axes: Sequence[Axis], w2d: torch.Tensor, dtype_in: int, dtype_out: int,
+                     pad: int = PAD_REPLICATE, pad_value: float = 0.0) -> N.fcfs_desc:
+    """Descriptor of the non-separable 2D layer: axes give r and s; K follows from w2d's taps."""
+    d = make_desc(shape, _full2d_axes(axes, w2d), dtype_in, dtype_out, pad, pad_value)
+    d.w2d = w2d.data_ptr()
+    d.w2d_per_channel = 1 if w2d.dim() == 5 else 0
+    return d
+
+
+def resize_full2d(x: torch.Tensor, axes: Sequence[Axis], w2d: torch.Tensor, pad: int = PAD_REPLICATE,
+                  pad_value: float = 0.0, out_dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+    """y = FCFS(x) with one general T_y x T_x kernel per phase pair (x [n, c, H, W] on a CUDA device)."""
+    if out_dtype is None:
+        out_dtype = torch.float32 if x.dtype == torch.uint8 else x.dtype
+    x = x.contiguous()
+    d = make_desc_full2d(x.shape, axes, w2d, _DT[x.dtype], _DT[out_dtype], pad, pad_value)
+    y = torch.empty(out_shape(x.shape, axes), dtype=out_dtype, device=x.device)
+    fcfs_forward(d, x.data_ptr(), y.data_ptr(), _stream(x.device))
+    return y
+
+
+def resize_full2d_backward(x: Optional[torch.Tensor], gy: torch.Tensor, axes: Sequence[Axis], w2d: torch.Tensor,
+                           pad: int = PAD_REPLICATE, pad_value: float = 0.0, in_shape=None, in_dtype=None,
+                           need_dx: bool = True, need_dw: bool = True):
+    """(gx, gw2d) of resize_full2d for upstream gradient gy."""
+    if in_shape is None:
+        in_shape = tuple(x.shape)
+    if in_dtype is None:
+        in_dtype = x.dtype
+    gy = gy.contiguous()
+    d = make_desc_full2d(in_shape, axes, w2d, _DT[in_dtype], _DT[gy.dtype], pad, pad_value)
+    dev = gy.device
+    gx = torch.empty(in_shape, dtype=in_dtype, device=dev) if need_dx else None
+    gw = torch.empty_like(w2d) if need_dw else None
+    ws_bytes = fcfs_backward_workspace(d) if need_dw else 0
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    fcfs_backward(d, x.data_ptr() if (x is not None and need_dw) else None, gy.data_ptr(),
+                  gx.data_ptr() if gx is not None else None, [gw.data_ptr() if gw is not None else None, None],
+                  ws.data_ptr(), ws_bytes, _stream(dev))
+    return gx, gw
+
+
+class FCFSFull2dFunction(torch.autograd.Function):
+    """Differentiable non-separable 2D FCFS: forward and both gradients in libfcfs kernels."""
+
+    @staticmethod
+    def forward(ctx, x, spec, w2d):
+        y = resize_full2d(x, spec["axes"], w2d, spec["pad"], spec["pad_value"], spec.get("out_dtype"))
+        ctx.spec = spec
+        ctx.save_for_backward(x, w2d)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, w2d = ctx.saved_tensors
+        spec = ctx.spec
+        need_w = ctx.needs_input_grad[2]
+        gx, gw = resize_full2d_backward(x, gy.to(spec.get("out_dtype") or x.dtype), spec["axes"], w2d, spec["pad"],
+                                        spec["pad_value"], in_shape=tuple(x.shape), in_dtype=x.dtype,
+                                        need_dx=ctx.needs_input_grad[0], need_dw=need_w)
+        return gx, None, gw
+
+
+class FCFSFull2d(torch.nn.Module):
+    """FCFS layer with learnable non-separable kernels: weight [C, r_y, r_x, T_y, T_x]
+    (or one shared [r_y, r_x, T_y, T_x]) initialised to the outer product of the
+    method's two axis tables, from which training may move to any 2D shape."""
+
+    def __init__(self, channels: int, ratios, method: int = BILINEAR, pad: int = PAD_REPLICATE,
+                 pad_value: float = 0.0, K: int = 0, per_channel: bool = True, out_dtype=None):
+        super().__init__()
+        (ry, sy), (rx, sx) = [tuple(rs) for rs in ratios]
+        wy, ky = fcfs_make_weights(method, ry, sy, K)
+        wx, kx = fcfs_make_weights(method, rx, sx, K)
+        w = np.einsum("am,bn->abmn", wy, wx).astype(np.float32)
+        if per_channel:
+            w = np.tile(w[None], (channels, 1, 1, 1, 1))
+        self.weight = torch.nn.Parameter(torch.from_numpy(np.ascontiguousarray(w)))
+        self.axes = [Axis(ry, sy, method, ky), Axis(rx, sx, method, kx)]
+        self.pad, self.pad_value, self.out_dtype = pad, pad_value, out_dtype
+
+    def forward(self, x):
+        spec = {"axes": self.axes, "pad": self.pad, "pad_value": self.pad_value, "out_dtype": self.out_dtype}
+        return FCFSFull2dFunction.apply(x, spec, self.weight.contiguous())
+
+
 # ----------------------------------------------------------------- serving
 
 class _DeviceArray:

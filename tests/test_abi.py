@@ -158,3 +158,37 @@ def test_backward_argument_errors(native):
     assert lib.fcfs_backward(ctypes.byref(d), BOGUS, BOGUS, None, ctypes.cast(gw, ctypes.c_void_p), None, 0,
                              None) == native.FCFS_ERR_ARG
     assert lib.fcfs_backward_workspace(ctypes.byref(d)) == 0
+
+
+def test_nonseparable_descriptor_errors(native):
+    """Validation of the non-separable 2D kernels (w2d); every case fails on the host before any device work."""
+    lib = native.load()
+    d = _desc(native, w2d=BOGUS, w2d_per_channel=1)
+    d.ndim = 3
+    d.in_shape[2] = d.out_shape[2] = 1
+    d.axis[2].r = d.axis[2].s = 1
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_ARG  # 2D only
+    d = _desc(native, w2d=BOGUS, w2d_per_channel=2)
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_ARG
+    d = _desc(native, w2d=BOGUS + 2, w2d_per_channel=0)
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_ARG  # misaligned weights
+    d = _desc(native, w2d=BOGUS, w2d_per_channel=0)
+    d.axis[0].w = BOGUS
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_ARG  # per-axis and w2d
+    d = _desc(native, w2d=BOGUS, w2d_per_channel=0)
+    d.axis[1].K = 5  # T = 11 > FCFS_MAX_TAPS
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_UNSUPPORTED
+    from paper_2203_10670_gb300 import fcfs
+
+    d = fcfs.make_desc((1, 1, 64, 64), [fcfs.Axis(8, 1, 1, 4), fcfs.Axis(8, 1, 1, 4)], 0, 0)
+    d.w2d, d.w2d_per_channel = BOGUS, 0  # 8 * 8 * 9 * 9 = 5184 kernel entries > 4096
+    assert lib.fcfs_forward(ctypes.byref(d), BOGUS, BOGUS, None) == native.FCFS_ERR_UNSUPPORTED
+    assert lib.fcfs_tune_forward(ctypes.byref(_desc(native, w2d=BOGUS)), BOGUS, BOGUS, None, 1, None,
+                                 None) == native.FCFS_ERR_UNSUPPORTED
+    d = _desc(native, w2d=BOGUS, w2d_per_channel=1)
+    gw = (ctypes.c_void_p * 3)(BOGUS, BOGUS, None)  # gw[1] must stay NULL
+    assert lib.fcfs_backward(ctypes.byref(d), BOGUS, BOGUS, None, ctypes.cast(gw, ctypes.c_void_p), None, 0,
+                             None) == native.FCFS_ERR_ARG
+    # partial-sum records: planes x chunks x (r_y r_x T_y T_x) floats, bilinear 3/2 -> T = 3
+    ws = lib.fcfs_backward_workspace(ctypes.byref(d))
+    assert ws > 0 and ws % (4 * 9 * 9) == 0
