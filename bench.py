@@ -58,6 +58,9 @@ def parse():
                         "input gradient of that c2 op (fp32), with --batch images")
     p.add_argument("--volume", action="store_true",
                    help="time only the c5 volume (1x1x256^3 fp32, trilinear 3/2): forward and input gradient")
+    p.add_argument("--full2d", action="store_true",
+                   help="time only the non-separable 5x5 learnable kernels on the c3 tensor (bf16, 5/4), "
+                        "with --batch images: forward, input gradient, both gradients")
     return p.parse_args()
 
 
@@ -401,8 +404,67 @@ def extras(fcfs, inputs, device, stream, peak, tune=True):
                     "bwd_dx_ms": tdx * 1e3, "bwd_dx_hbm_frac": nb / tdx / 1e9 / peak}
         del x5, y5
     torch.cuda.empty_cache()
+    for k, v in full2d_times(fcfs, inputs, device, stream, peak).items():
+        out[f"f2_nonseparable_5x5_bf16_{k}"] = v
+    torch.cuda.empty_cache()
     out.update(serve_bench(fcfs, inputs, device))
     return out
+
+
+# FP32 FMA peak of the non-tensor path: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def full2d_times(fcfs, inputs, device, stream, peak, batch=None, steps=5, warmup=1):
+    """Non-separable learnable kernels (one 5x5 kernel per phase pair and channel, 64x5x5x5x5) on the
+    c3 tensor, 8x64x256^2 bf16 resized 5/4 on both axes: forward, input gradient, both gradients.
+    The kernel starts as the outer product of the bilinear 5/4 tables."""
+    s3 = tuple(inputs.C3["shape"])
+    if batch:
+        s3 = (batch,) + s3[1:]
+    W, K = fcfs.fcfs_make_weights(fcfs.BILINEAR, 5, 4)
+    w2d = np.tile(np.einsum("am,bn->abmn", W, W)[None], (s3[1], 1, 1, 1, 1)).astype(np.float32)
+    w2d = torch.from_numpy(np.ascontiguousarray(w2d)).to(device)
+    ax = [fcfs.Axis(5, 4, fcfs.BILINEAR, K)] * 2
+    x = inputs.normal(s3, inputs.C3["seed"], device=device, dtype=torch.bfloat16)
+    y = fcfs.resize_full2d(x, ax, w2d)
+    g = inputs.normal(tuple(y.shape), inputs.C3["grad_seed"], device=device, dtype=torch.bfloat16)
+
+    def fwd():
+        fcfs.resize_full2d(x, ax, w2d, out=y)
+
+    def dx():
+        fcfs.resize_full2d_backward(x, g, ax, w2d, need_dx=True, need_dw=False)
+
+    def dxdw():
+        fcfs.resize_full2d_backward(x, g, ax, w2d, need_dx=True, need_dw=True)
+
+    for _ in range(max(1, warmup)):
+        fwd(), dx(), dxdw()
+    out = {}
+    px = s3[0] * y.shape[2] * y.shape[3]
+    TT = (2 * K + 1) ** 2
+    flop = 2.0 * TT * y.numel()  # one FMA per (output, tap) pair
+    for key, fn, nbytes, nflop in (("fwd", fwd, (x.numel() + y.numel()) * 2, flop),
+                                   ("bwd_dx", dx, (x.numel() + y.numel()) * 2, flop),
+                                   ("bwd_dx_dw", dxdw, (2 * x.numel() + 2 * y.numel()) * 2, 2 * flop)):
+        t = timed(fn, steps, stream) / steps
+        out[key] = {"ms": t * 1e3, "Gpix_s": px / t / 1e9, "hbm_frac": nbytes / t / 1e9 / peak,
+                    "alu_frac": nflop / t / 1e12 / FP32_ALU_TFLOPS}
+    return out
+
+
+def full2d_only(args, device):
+    from paper_2203_10670_gb300 import build as B
+
+    B.build()
+    from paper_2203_10670_gb300 import fcfs, inputs
+
+    stream = torch.cuda.current_stream(device)
+    peak, _ = peaks()
+    r = full2d_times(fcfs, inputs, device, stream, peak, batch=args.batch if args.batch != 16 else None,
+                     steps=args.steps, warmup=args.warmup)
+    print(json.dumps({"mode": "non-separable 5x5 learnable kernels, c3 tensor bf16 5/4", **r}), flush=True)
 
 
 def serve_bench(fcfs, inputs, device, count=None):
@@ -531,6 +593,9 @@ def main():
             return
         if args.volume:
             volume_only(args, device)
+            return
+        if args.full2d:
+            full2d_only(args, device)
             return
         run_ours(args, rank, world, device)
     finally:

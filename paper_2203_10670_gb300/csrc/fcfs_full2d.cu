@@ -4,14 +4,19 @@
 // the interpolation kernel (Sec. 6):
 //   y[n,c, iy r_y + jy, ix r_x + jx] = sum_{my,mx} W[c][jy][jx][my][mx]
 //                                      x~[n,c, iy s_y - L_y + my, ix s_x - L_x + mx]
-//   K7 fcfs_full2d_fwd       - padded input tile staged through the index map,
-//                              NPH phases of one window per thread, kernel
+//   K7 fcfs_full2d_fwd       - padded input tile staged through the index map
+//                              with its columns split by residue mod s_x (the
+//                              windows of a warp then read consecutive words),
+//                              NPH phases of two windows per thread, kernel
 //                              weights as shared-memory broadcasts;
 //   K8 fcfs_full2d_dx        - input gradient: for every extended index the
 //                              windows and taps reaching it are gathered from a
-//                              phase-major g tile, then the pad adjoint folds
-//                              the virtual cells into the real ones;
-//   K9 fcfs_full2d_dw        - weight-gradient partials (one record per CTA),
+//                              phase-major g tile, four phases per step, then
+//                              the pad adjoint folds the virtual cells into the
+//                              real ones;
+//   K9 fcfs_full2d_dw        - weight-gradient partials, each thread a 4-phase
+//                              x 4-tap block of outer products over its share of
+//                              the windows (one record per CTA),
 //      fcfs_full2d_dw_reduce - fixed-order FP64 reduction of the records.
 // No atomics anywhere: every result is bitwise reproducible run to run.
 #include <algorithm>
@@ -27,7 +32,7 @@ namespace {
 
 constexpr int kF2MaxExtra = 48;  // pad-fold entries per axis (virtual index -> real index)
 constexpr int kF2MaxEntries = 4096;  // r_y r_x T_y T_x per channel
-constexpr int kF2MaxEPT = kF2MaxEntries / 256;
+constexpr int kF2FwdWX = 64;  // windows per forward tile row: two per lane
 
 struct F2Axis {
     int n_in, n_out, r, s, T, L, nw;  // nw = ceil(n_out / r) windows
@@ -53,6 +58,7 @@ struct F2Params {
     int tiles_x, tiles_y;
     int VYc, VXc, NWYc, NWXc;  // input gradient: capacities of the virtual range and of the window range
     int nchunk, ngroups;       // weight gradient: records per plane, window groups per CTA
+    int npass;                 // weight gradient: CTAs per (plane, chunk) when the blocks exceed one CTA
 };
 
 __device__ __forceinline__ int pmod(int a, int b) {
@@ -72,6 +78,44 @@ __device__ __forceinline__ void f2_stage_weights(float* dst, const F2Params& p, 
     }
 }
 
+// Input tile [rows][cols] (extended coordinates row0/col0, padding as an
+// index map) with each row's columns split by residue mod s: column col is
+// stored at (col mod s) * KW + col / s.  Windows ix = 0, 1, ... read columns
+// ix*s + m, which then sit at consecutive words.  One warp per row.
+template <typename Tin>
+__device__ __forceinline__ void f2_load_tile_split(float* dst, int pitch, int KW, int s, const Tin* src_plane, int H,
+                                                   int W, int row0, int col0, int rows, int cols, int pad,
+                                                   float padv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int q32 = 32 / s, u32 = 32 - q32 * s;
+    const int q0 = lane / s, u0 = lane - q0 * s;
+    const bool inside_x = col0 >= 0 && col0 + cols <= W;
+    for (int ry = warp; ry < rows; ry += nwarp) {
+        const int sy = ext_index(row0 + ry, H, pad);
+        float* d = dst + ry * pitch;
+        const Tin* src = sy >= 0 ? src_plane + (long long)sy * W : nullptr;
+        int q = q0, u = u0;
+        for (int cx = lane; cx < cols; cx += 32) {
+            float v = padv;
+            if (src != nullptr) {
+                if (inside_x) {
+                    v = load_f(src + col0 + cx);
+                } else {
+                    const int sx = ext_index(col0 + cx, W, pad);
+                    if (sx >= 0) v = load_f(src + sx);
+                }
+            }
+            d[u * KW + q] = v;
+            q += q32;
+            u += u32;
+            if (u >= s) {
+                u -= s;
+                ++q;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ forward
 
 template <int NPH, typename Tin, typename Tout>
@@ -86,52 +130,71 @@ __global__ void __launch_bounds__(256) fcfs_full2d_fwd(const __grid_constant__ F
     const int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
     const int c = (int)(plane % p.C);
     const int iy0 = ty * p.WY, ix0 = tx * p.WX;
-    const int TT = AY.T * AX.T;
+    const int TT = AY.T * AX.T, TX = AX.T, Ppad = p.Ppad;
     const int rows = (p.WY - 1) * AY.s + AY.T, cols = (p.WX - 1) * AX.s + AX.T;
-    float* sIn = sW + TT * p.Ppad;
+    const int KW = (cols + AX.s - 1) / AX.s, pitch = KW * AX.s;
+    float* sIn = sW + TT * Ppad;
 
     f2_stage_weights(sW, p, c);
     const Tin* xp = reinterpret_cast<const Tin*>(p.x) + plane * (long long)AY.n_in * AX.n_in;
-    load_tile<Tin>(sIn, cols, xp, AY.n_in, AX.n_in, iy0 * AY.s - AY.L, ix0 * AX.s - AX.L, rows, cols, p.pad, p.padv);
+    f2_load_tile_split<Tin>(sIn, pitch, KW, AX.s, xp, AY.n_in, AX.n_in, iy0 * AY.s - AY.L, ix0 * AX.s - AX.L, rows,
+                            cols, p.pad, p.padv);
     __syncthreads();
 
     Tout* yp = reinterpret_cast<Tout*>(p.y) + plane * (long long)AY.n_out * AX.n_out;
-    const int nch = p.Ppad / NPH;
-    const int items = p.WY * nch * p.WX;
+    const int nch = Ppad / NPH;
+    const int items = p.WY * nch * 32;  // lane l: windows l and l + 32 of the tile row
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int ixl = it % p.WX, rest = it / p.WX;
+        const int ixl = it & 31, rest = it >> 5;
         const int ch = rest % nch, iyl = rest / nch;
-        const int iy = iy0 + iyl, ix = ix0 + ixl;
-        if (iy >= AY.nw || ix >= AX.nw) continue;
-        float acc[NPH];
+        const int iy = iy0 + iyl, ixa = ix0 + ixl, ixb = ixa + 32;
+        if (iy >= AY.nw || ixa >= AX.nw) continue;
+        float a[NPH], b[NPH];
 #pragma unroll
-        for (int k = 0; k < NPH; ++k) acc[k] = 0.f;
-        const float* src = sIn + iyl * AY.s * cols + ixl * AX.s;
+        for (int k = 0; k < NPH; ++k) a[k] = b[k] = 0.f;
+        const float* src = sIn + iyl * AY.s * pitch + ixl;
         const float* wp = sW + ch * NPH;
         for (int my = 0; my < AY.T; ++my) {
-            for (int mx = 0; mx < AX.T; ++mx) {
-                const float v = src[mx];
+            // tap mx sits at (mx mod s) * KW + mx / s of the split row
+            int off = 0, u = 0;
+            const float* wq = wp;
+            for (int mx = 0; mx < TX; ++mx) {
+                const float v0 = src[off], v1 = src[off + 32];
+                float w[NPH];
                 if constexpr (NPH == 4) {
-                    const float4 w4 = *reinterpret_cast<const float4*>(wp);
-                    acc[0] = fmaf(w4.x, v, acc[0]);
-                    acc[1] = fmaf(w4.y, v, acc[1]);
-                    acc[2] = fmaf(w4.z, v, acc[2]);
-                    acc[3] = fmaf(w4.w, v, acc[3]);
+                    const float4 w4 = *reinterpret_cast<const float4*>(wq);
+                    w[0] = w4.x, w[1] = w4.y, w[2] = w4.z, w[3] = w4.w;
                 } else {
 #pragma unroll
-                    for (int k = 0; k < NPH; ++k) acc[k] = fmaf(wp[k], v, acc[k]);
+                    for (int k = 0; k < NPH; ++k) w[k] = wq[k];
                 }
-                wp += p.Ppad;
+#pragma unroll
+                for (int k = 0; k < NPH; ++k) {
+                    a[k] = fmaf(w[k], v0, a[k]);
+                    b[k] = fmaf(w[k], v1, b[k]);
+                }
+                wq += Ppad;
+                off += KW;
+                if (++u == AX.s) {
+                    u = 0;
+                    off += 1 - AX.s * KW;
+                }
             }
-            src += cols;
+            src += pitch;
+            wp += TX * Ppad;
         }
 #pragma unroll
         for (int k = 0; k < NPH; ++k) {
             const int ph = ch * NPH + k;
             if (ph < p.P) {
                 const int jy = ph / AX.r, jx = ph - jy * AX.r;
-                const int oy = iy * AY.r + jy, ox = ix * AX.r + jx;
-                if (oy < AY.n_out && ox < AX.n_out) store_f(yp + (long long)oy * AX.n_out + ox, acc[k]);
+                const int oy = iy * AY.r + jy;
+                if (oy < AY.n_out) {
+                    Tout* row = yp + (long long)oy * AX.n_out;
+                    const int oxa = ixa * AX.r + jx, oxb = ixb * AX.r + jx;
+                    if (oxa < AX.n_out) store_f(row + oxa, a[k]);
+                    if (ixb < AX.nw && oxb < AX.n_out) store_f(row + oxb, b[k]);
+                }
             }
         }
     }
@@ -170,9 +233,10 @@ __global__ void __launch_bounds__(256) fcfs_full2d_dx(const __grid_constant__ F2
     const int c = (int)(plane % p.C);
     const int qy0 = ty * p.WY, qx0 = tx * p.WX;
     const int qy1 = imin(qy0 + p.WY, AY.n_in), qx1 = imin(qx0 + p.WX, AX.n_in);
-    const int TT = AY.T * AX.T, P = p.P;
-    float* sG = sW + TT * p.Ppad;
-    float* sV = sG + P * p.NWYc * p.NWXc;
+    const int TT = AY.T * AX.T, Ppad = p.Ppad;
+    const int gplane = p.NWYc * p.NWXc;
+    float* sG = sW + TT * Ppad;
+    float* sV = sG + Ppad * gplane;
 
     int vylo, vyhi, vxlo, vxhi;
     bool fy, fx;
@@ -183,42 +247,83 @@ __global__ void __launch_bounds__(256) fcfs_full2d_dx(const __grid_constant__ F2
     const int wxlo = -floordiv(-(vxlo + AX.L - AX.T + 1), AX.s), wxhi = floordiv(vxhi + AX.L, AX.s);
     const int nwx = wxhi - wxlo + 1;
     const int VY = vyhi - vylo + 1, VX = vxhi - vxlo + 1;
-    const int gplane = p.NWYc * p.NWXc;
 
     f2_stage_weights(sW, p, c);
     // g tile, phase-major: sG[ph][iy - wylo][ix - wxlo]; zero outside the output
+    // and on the padding phases [P, Ppad)
     const Tg* gp = reinterpret_cast<const Tg*>(p.g) + plane * (long long)AY.n_out * AX.n_out;
     {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
         const int grow = (wyhi - wylo + 1) * AY.r, gcol = nwx * AX.r;
         const int oy0 = wylo * AY.r, ox0 = wxlo * AX.r;
-        for (int k = threadIdx.x; k < grow * gcol; k += blockDim.x) {
-            const int rr = k / gcol, cc = k - rr * gcol;
-            const int oy = oy0 + rr, ox = ox0 + cc;
-            float v = 0.f;
-            if (oy >= 0 && oy < AY.n_out && ox >= 0 && ox < AX.n_out) v = load_f(gp + (long long)oy * AX.n_out + ox);
+        const int q32 = 32 / AX.r, u32 = 32 - q32 * AX.r;
+        const int q0 = lane / AX.r, u0 = lane - q0 * AX.r;
+        for (int rr = warp; rr < grow; rr += nwarp) {
+            const int oy = oy0 + rr;
             const int iyl = rr / AY.r, jy = rr - iyl * AY.r;
-            const int ixl = cc / AX.r, jx = cc - ixl * AX.r;
-            sG[(jy * AX.r + jx) * gplane + iyl * p.NWXc + ixl] = v;
+            const bool row_ok = oy >= 0 && oy < AY.n_out;
+            const Tg* grow_p = gp + (long long)oy * AX.n_out;
+            float* dst = sG + jy * AX.r * gplane + iyl * p.NWXc;
+            int ixl = q0, jx = u0;
+            for (int cc = lane; cc < gcol; cc += 32) {
+                const int ox = ox0 + cc;
+                float v = 0.f;
+                if (row_ok && ox >= 0 && ox < AX.n_out) v = load_f(grow_p + ox);
+                dst[jx * gplane + ixl] = v;
+                ixl += q32;
+                jx += u32;
+                if (jx >= AX.r) {
+                    jx -= AX.r;
+                    ++ixl;
+                }
+            }
         }
+        for (int k = p.P * gplane + threadIdx.x; k < Ppad * gplane; k += blockDim.x) sG[k] = 0.f;
     }
     __syncthreads();
 
-    // virtual cells: sV[ey - vylo][ex - vxlo] = sum over (window, phase, tap) reaching (ey, ex)
-    for (int k = threadIdx.x; k < VY * VX; k += blockDim.x) {
-        const int vyl = k / VX, vxl = k - vyl * VX;
-        const int dy = vylo + vyl + AY.L, dxv = vxlo + vxl + AX.L;
-        const int uy = pmod(dy, AY.s), ux = pmod(dxv, AX.s);
-        float acc = 0.f;
-        for (int my = uy; my < AY.T; my += AY.s) {
-            const int iyl = (dy - my) / AY.s - wylo;
-            for (int mx = ux; mx < AX.T; mx += AX.s) {
-                const int ixl = (dxv - mx) / AX.s - wxlo;
-                const float* wv = sW + (my * AX.T + mx) * p.Ppad;
-                const float* gv = sG + iyl * p.NWXc + ixl;
-                for (int ph = 0; ph < P; ++ph) acc = fmaf(wv[ph], gv[ph * gplane], acc);
+    // virtual cells: sV[ey - vylo][ex - vxlo] = sum over (window, phase, tap)
+    // reaching (ey, ex).  Tap my reaches ey from window (ey + L - my) / s when
+    // my = (ey + L) mod s (mod s); one warp per row, lanes across the row.
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        const int dx0 = vxlo + lane + AX.L;
+        const int ux0 = pmod(dx0, AX.s), ix0l = (dx0 - ux0) / AX.s - wxlo;
+        const int q32 = 32 / AX.s, u32 = 32 - q32 * AX.s;
+        for (int vyl = warp; vyl < VY; vyl += nwarp) {
+            const int dy = vylo + vyl + AY.L;
+            const int uy = pmod(dy, AY.s), iy0l = (dy - uy) / AY.s - wylo;
+            int ux = ux0, ixs = ix0l;
+            for (int vxl = lane; vxl < VX; vxl += 32) {
+                float acc0 = 0.f, acc1 = 0.f;
+                int iyl = iy0l;
+                for (int my = uy; my < AY.T; my += AY.s, --iyl) {
+                    int ixl = ixs;
+                    const float* wrow = sW + my * AX.T * Ppad;
+                    const float* grow_s = sG + iyl * p.NWXc;
+                    for (int mx = ux; mx < AX.T; mx += AX.s, --ixl) {
+                        const float4* wv = reinterpret_cast<const float4*>(wrow + mx * Ppad);
+                        const float* gv = grow_s + ixl;
+                        for (int ph = 0; ph < Ppad; ph += 4) {
+                            const float4 w = *wv++;
+                            acc0 = fmaf(w.x, gv[0], acc0);
+                            acc1 = fmaf(w.y, gv[gplane], acc1);
+                            acc0 = fmaf(w.z, gv[2 * gplane], acc0);
+                            acc1 = fmaf(w.w, gv[3 * gplane], acc1);
+                            gv += 4 * gplane;
+                        }
+                    }
+                }
+                sV[vyl * p.VXc + vxl] = acc0 + acc1;
+                // next cell of this lane: 32 columns on
+                ixs += q32;
+                ux += u32;
+                if (ux >= AX.s) {
+                    ux -= AX.s;
+                    ++ixs;
+                }
             }
         }
-        sV[vyl * p.VXc + vxl] = acc;
     }
     __syncthreads();
 
@@ -257,94 +362,139 @@ __global__ void __launch_bounds__(256) fcfs_full2d_dx(const __grid_constant__ F2
 
 // ---------------------------------------------------------- weight gradient
 
+// dW[ph][t] = sum over windows of g[window][ph] * x~[window origin + tap t]: a
+// (phases x windows) by (windows x taps) product.  Each thread owns a block of
+// 4 phases x 4 taps and runs over every G-th window of each staged tile.
 template <typename Tx, typename Tg>
 __global__ void __launch_bounds__(256) fcfs_full2d_dw(const __grid_constant__ F2Params p) {
     extern __shared__ float4 f2_smem4[];
-    float* sIn = reinterpret_cast<float*>(f2_smem4);
     const F2Axis& AY = p.ax[0];
     const F2Axis& AX = p.ax[1];
-    const long long plane = blockIdx.x / p.nchunk;
-    const int chunk = (int)(blockIdx.x - plane * p.nchunk);
+    const int pass = (int)(blockIdx.x % p.npass);
+    const long long pc = blockIdx.x / p.npass;
+    const long long plane = pc / p.nchunk;
+    const int chunk = (int)(pc - plane * p.nchunk);
     const int ntiles = p.tiles_x * p.tiles_y;
-    const int TT = AY.T * AX.T, E = p.E;
+    const int TT = AY.T * AX.T, TX = AX.T, Ppad = p.Ppad;
     const int rows = (p.WY - 1) * AY.s + AY.T, cols = (p.WX - 1) * AX.s + AX.T;
-    const int gpitch = p.WX * AX.r, grows = p.WY * AY.r;
-    float* sG = sIn + rows * cols;
-    float* sRed = sG + grows * gpitch;
+    const int KW = (cols + AX.s - 1) / AX.s, pitch = KW * AX.s;
+    const int NTB = (TT + 3) >> 2, NPB = Ppad >> 2, nblk = NPB * NTB;
+    float* sG = reinterpret_cast<float*>(f2_smem4);  // [WY*WX windows][Ppad], 16-byte aligned rows
+    float* sIn = sG + p.WY * p.WX * Ppad;
+    float* sRed = sIn + rows * pitch;
 
-    // entries of this thread: one entry and a window group when E <= 256,
-    // else entries e0 + 256 k over every window
-    int G, grp, e0, ept;
-    if (E <= 256) {
+    int G, grp, blk;
+    if (p.npass == 1) {
         G = p.ngroups;
-        grp = threadIdx.x / E;
-        e0 = threadIdx.x - grp * E;
-        ept = grp < G ? 1 : 0;
+        grp = threadIdx.x / nblk;
+        blk = threadIdx.x - grp * nblk;
     } else {
         G = 1;
         grp = 0;
-        e0 = threadIdx.x;
-        ept = (E - (int)threadIdx.x + 255) / 256;
+        blk = pass * 256 + threadIdx.x;
     }
-    int xoff[kF2MaxEPT], goff[kF2MaxEPT];
-    float acc[kF2MaxEPT];
+    const bool active = grp < G && blk < nblk;
+    const int pb = active ? blk / NTB : 0, tb = active ? blk - (blk / NTB) * NTB : 0;
+    int xoff[4];
 #pragma unroll
-    for (int k = 0; k < kF2MaxEPT; ++k) {
-        acc[k] = 0.f;
-        int xo = 0, go = 0;
-        if (k < ept) {
-            const int e = e0 + 256 * k;
-            const int ph = e / TT, tap = e - ph * TT;
-            const int my = tap / AX.T, mx = tap - my * AX.T;
-            const int jy = ph / AX.r, jx = ph - jy * AX.r;
-            xo = my * cols + mx;
-            go = jy * gpitch + jx;
+    for (int k = 0; k < 4; ++k) {
+        const int t = tb * 4 + k;
+        int o = 0;
+        if (t < TT) {
+            const int my = t / TX, mx = t - my * TX, q = mx / AX.s;
+            o = my * pitch + (mx - q * AX.s) * KW + q;
         }
-        xoff[k] = xo;
-        goff[k] = go;
+        xoff[k] = o;
     }
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
 
     const Tx* xp = reinterpret_cast<const Tx*>(p.x) + plane * (long long)AY.n_in * AX.n_in;
     const Tg* gp = reinterpret_cast<const Tg*>(p.g) + plane * (long long)AY.n_out * AX.n_out;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int q32 = 32 / AX.r, u32 = 32 - q32 * AX.r;
+    const int q0 = lane / AX.r, u0 = lane - q0 * AX.r;
     for (int tile = chunk; tile < ntiles; tile += p.nchunk) {
         const int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
         const int iy0 = ty * p.WY, ix0 = tx * p.WX;
         __syncthreads();  // the previous tile's reads are done
-        load_tile<Tx>(sIn, cols, xp, AY.n_in, AX.n_in, iy0 * AY.s - AY.L, ix0 * AX.s - AX.L, rows, cols, p.pad,
-                      p.padv);
-        const int oy0 = iy0 * AY.r, ox0 = ix0 * AX.r;
-        for (int k = threadIdx.x; k < grows * gpitch; k += blockDim.x) {
-            const int rr = k / gpitch, cc = k - rr * gpitch;
-            const int oy = oy0 + rr, ox = ox0 + cc;
-            sG[k] = (oy < AY.n_out && ox < AX.n_out) ? load_f(gp + (long long)oy * AX.n_out + ox) : 0.f;
+        f2_load_tile_split<Tx>(sIn, pitch, KW, AX.s, xp, AY.n_in, AX.n_in, iy0 * AY.s - AY.L, ix0 * AX.s - AX.L,
+                               rows, cols, p.pad, p.padv);
+        // g tile, window-major: sG[(iyl*WX + ixl)*Ppad + jy*r_x + jx]; zero outside the output
+        const int oy0 = iy0 * AY.r, ox0 = ix0 * AX.r, gcol = p.WX * AX.r;
+        for (int rr = warp; rr < p.WY * AY.r; rr += nwarp) {
+            const int oy = oy0 + rr;
+            const int iyl = rr / AY.r, jy = rr - iyl * AY.r;
+            const bool row_ok = oy < AY.n_out;
+            const Tg* grow_p = gp + (long long)oy * AX.n_out;
+            float* dst = sG + iyl * p.WX * Ppad + jy * AX.r;
+            int ixl = q0, jx = u0;
+            for (int cc = lane; cc < gcol; cc += 32) {
+                const int ox = ox0 + cc;
+                dst[ixl * Ppad + jx] = (row_ok && ox < AX.n_out) ? load_f(grow_p + ox) : 0.f;
+                ixl += q32;
+                jx += u32;
+                if (jx >= AX.r) {
+                    jx -= AX.r;
+                    ++ixl;
+                }
+            }
         }
         __syncthreads();
-        if (ept == 0) continue;
+        if (!active) continue;
         const int nwy = imin(p.WY, AY.nw - iy0), nwx = imin(p.WX, AX.nw - ix0);
-        const int nwin = nwy * nwx;
-        for (int w = grp; w < nwin; w += G) {
-            const int iyl = w / nwx, ixl = w - iyl * nwx;
-            const float* xs = sIn + iyl * AY.s * cols + ixl * AX.s;
-            const float* gs = sG + iyl * AY.r * gpitch + ixl * AX.r;
+        int iyl = 0, ixl = grp;
+        while (ixl >= nwx && iyl < nwy) {
+            ixl -= nwx;
+            ++iyl;
+        }
+        while (iyl < nwy) {
+            const float* xw = sIn + iyl * AY.s * pitch + ixl;
+            const float4 g4 = *reinterpret_cast<const float4*>(sG + (iyl * p.WX + ixl) * Ppad + pb * 4);
+            const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+            float xv[4];
 #pragma unroll
-            for (int k = 0; k < kF2MaxEPT; ++k)
-                if (k < ept) acc[k] = fmaf(gs[goff[k]], xs[xoff[k]], acc[k]);
+            for (int k = 0; k < 4; ++k) xv[k] = xw[xoff[k]];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(gv[i], xv[k], acc[i][k]);
+            ixl += G;
+            while (ixl >= nwx) {
+                ixl -= nwx;
+                ++iyl;
+            }
         }
     }
 
-    float* rec = p.ws + (plane * p.nchunk + chunk) * (long long)E;
-    if (E <= 256) {
-        if (ept) sRed[grp * E + e0] = acc[0];
-        __syncthreads();
-        if ((int)threadIdx.x < E) {
-            float s = 0.f;
-            for (int g = 0; g < G; ++g) s += sRed[g * E + threadIdx.x];
-            rec[threadIdx.x] = s;
-        }
-    } else {
+    float* rec = p.ws + pc * (long long)p.E;
+    if (p.npass == 1) {
+        // fixed-order sum over the window groups: sRed[grp][ph][t] on the padded grid
+        const int PT = NTB * 4;
+        if (active) {
 #pragma unroll
-        for (int k = 0; k < kF2MaxEPT; ++k)
-            if (k < ept) rec[e0 + 256 * k] = acc[k];
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) sRed[(grp * Ppad + pb * 4 + i) * PT + tb * 4 + k] = acc[i][k];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < p.E; e += blockDim.x) {
+            const int ph = e / TT, t = e - ph * TT;
+            float s = 0.f;
+            for (int g = 0; g < G; ++g) s += sRed[(g * Ppad + ph) * PT + t];
+            rec[e] = s;
+        }
+    } else if (active) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int ph = pb * 4 + i, t = tb * 4 + k;
+                if (ph < p.P && t < TT) rec[ph * TT + t] = acc[i][k];
+            }
     }
 }
 
@@ -419,9 +569,16 @@ int f2_params(const fcfs_desc* d, F2Params* p) {
     return FCFS_OK;
 }
 
+size_t f2_pitch(const F2Params& p, int* rows) {
+    *rows = (p.WY - 1) * p.ax[0].s + p.ax[0].T;
+    const int cols = (p.WX - 1) * p.ax[1].s + p.ax[1].T;
+    return (size_t)((cols + p.ax[1].s - 1) / p.ax[1].s) * p.ax[1].s;
+}
+
 size_t f2_fwd_smem(const F2Params& p) {
-    const int rows = (p.WY - 1) * p.ax[0].s + p.ax[0].T, cols = (p.WX - 1) * p.ax[1].s + p.ax[1].T;
-    return sizeof(float) * ((size_t)p.ax[0].T * p.ax[1].T * p.Ppad + (size_t)rows * cols);
+    int rows;
+    const size_t pitch = f2_pitch(p, &rows);
+    return sizeof(float) * ((size_t)p.ax[0].T * p.ax[1].T * p.Ppad + (size_t)rows * pitch);
 }
 
 // Capacity of the virtual range of any tile of Q real cells along one axis,
@@ -445,13 +602,16 @@ void f2_axis_caps(const F2Axis& A, int Q, int* Vc, int* NWc) {
 }
 
 size_t f2_dx_smem(const F2Params& p) {
-    return sizeof(float) * ((size_t)p.ax[0].T * p.ax[1].T * p.Ppad + (size_t)p.P * p.NWYc * p.NWXc +
+    return sizeof(float) * ((size_t)p.ax[0].T * p.ax[1].T * p.Ppad + (size_t)p.Ppad * p.NWYc * p.NWXc +
                             (size_t)p.VYc * p.VXc);
 }
 
+// window-major g tile, split input tile, and the group-reduction area (at most
+// 256 threads x 16 partial sums)
 size_t f2_dw_smem(const F2Params& p) {
-    const int rows = (p.WY - 1) * p.ax[0].s + p.ax[0].T, cols = (p.WX - 1) * p.ax[1].s + p.ax[1].T;
-    return sizeof(float) * ((size_t)rows * cols + (size_t)p.WY * p.ax[0].r * p.WX * p.ax[1].r + 256);
+    int rows;
+    const size_t pitch = f2_pitch(p, &rows);
+    return sizeof(float) * ((size_t)p.WY * p.WX * p.Ppad + (size_t)rows * pitch + 256 * 16);
 }
 
 constexpr size_t kF2SmemCap = 200 * 1024;
@@ -466,17 +626,18 @@ cudaError_t f2_launch(K kernel, const F2Params& p, long long blocks, size_t smem
     return cudaGetLastError();
 }
 
-// Window tile of the forward / weight-gradient kernels: 32 windows across
-// (one warp), rows shrunk until the staged tile fits.
+// Window tile of the forward / weight-gradient kernels: WX windows across
+// (the forward's lanes take two windows each), rows shrunk until the staged
+// tile fits.
 int f2_window_tile(F2Params& p, bool for_dw) {
-    p.WX = 32;
+    p.WX = for_dw ? 32 : kF2FwdWX;
     p.WY = 8;
     for (;;) {
         const size_t smem = for_dw ? f2_dw_smem(p) : f2_fwd_smem(p);
         if (smem <= kF2SmemCap) break;
         if (p.WY > 1) {
             p.WY /= 2;
-        } else if (p.WX > 1) {
+        } else if (for_dw && p.WX > 1) {
             p.WX /= 2;
         } else {
             return fail(FCFS_ERR_UNSUPPORTED, "non-separable kernel tile exceeds shared memory");
@@ -525,16 +686,19 @@ int full2d_forward(const fcfs_desc* d, const void* x, void* y, cudaStream_t st) 
 static int f2_dw_plan(const fcfs_desc* d, F2Params* p) {
     int rc = f2_params(d, p);
     if (rc) return rc;
-    p->Ppad = p->P;
+    p->Ppad = (p->P + 3) / 4 * 4;
     rc = f2_window_tile(*p, true);
     if (rc) return rc;
     const int ntiles = p->tiles_x * p->tiles_y;
+    const int TT = p->ax[0].T * p->ax[1].T;
+    const int nblk = (p->Ppad / 4) * ((TT + 3) / 4);
+    p->ngroups = nblk <= 256 ? 256 / nblk : 1;
+    p->npass = nblk <= 256 ? 1 : (nblk + 255) / 256;
     // enough CTAs for four per SM, records capped near 8 MiB where the plane count allows
     const long long want = (608 + p->planes - 1) / std::max(1LL, p->planes);
     const long long cap = std::max(1LL, (8LL << 20) / (4LL * p->E * std::max(1LL, p->planes)));
     p->nchunk = (int)std::max(1LL, std::min({want, cap, (long long)ntiles}));
-    p->ngroups = p->E <= 256 ? 256 / p->E : 1;
-    if ((long long)p->nchunk * p->planes > INT_MAX) return fail(FCFS_ERR_UNSUPPORTED, "grid too large");
+    if ((long long)p->nchunk * p->planes * p->npass > INT_MAX) return fail(FCFS_ERR_UNSUPPORTED, "grid too large");
     return FCFS_OK;
 }
 
@@ -550,7 +714,7 @@ int full2d_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx,
         F2Params p;
         int rc = f2_params(d, &p);
         if (rc) return rc;
-        p.Ppad = p.P;
+        p.Ppad = (p.P + 3) / 4 * 4;
         int Q = 32;
         for (;;) {
             p.WX = p.WY = Q;
@@ -587,7 +751,7 @@ int full2d_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx,
         p.g = gy;
         p.ws = (float*)ws;
         p.dw = gw;
-        const long long blocks = (long long)p.nchunk * p.planes;
+        const long long blocks = (long long)p.nchunk * p.planes * p.npass;
         const size_t smem = f2_dw_smem(p);
         cudaError_t e;
         if (d->dtype_in == FCFS_F32) {

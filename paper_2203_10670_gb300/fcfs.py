@@ -301,15 +301,20 @@ def make_desc_full2d(shape: Sequence[int], axes: Sequence[Axis], w2d: torch.Tens
 
 
 def resize_full2d(x: torch.Tensor, axes: Sequence[Axis], w2d: torch.Tensor, pad: int = PAD_REPLICATE,
-                  pad_value: float = 0.0, out_dtype: Optional[torch.dtype] = None) -> torch.Tensor:
+                  pad_value: float = 0.0, out_dtype: Optional[torch.dtype] = None,
+                  out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """y = FCFS(x) with one general T_y x T_x kernel per phase pair (x [n, c, H, W] on a CUDA device)."""
     if out_dtype is None:
-        out_dtype = torch.float32 if x.dtype == torch.uint8 else x.dtype
+        out_dtype = out.dtype if out is not None else torch.float32 if x.dtype == torch.uint8 else x.dtype
     x = x.contiguous()
     d = make_desc_full2d(x.shape, axes, w2d, _DT[x.dtype], _DT[out_dtype], pad, pad_value)
-    y = torch.empty(out_shape(x.shape, axes), dtype=out_dtype, device=x.device)
-    fcfs_forward(d, x.data_ptr(), y.data_ptr(), _stream(x.device))
-    return y
+    oshape = out_shape(x.shape, axes)
+    if out is None:
+        out = torch.empty(oshape, dtype=out_dtype, device=x.device)
+    elif tuple(out.shape) != oshape or out.dtype != out_dtype or not out.is_contiguous():
+        raise ValueError("out has the wrong shape, dtype or layout")
+    fcfs_forward(d, x.data_ptr(), out.data_ptr(), _stream(x.device))
+    return out
 
 
 def resize_full2d_backward(x: Optional[torch.Tensor], gy: torch.Tensor, axes: Sequence[Axis], w2d: torch.Tensor,
