@@ -6,17 +6,20 @@
 // relative to the tile's first adjoint window, so whole windows are written
 // without bounds tests; edge tiles fold the virtual indices as the
 // per-output kernel does.
+#include <type_traits>
+
 #include "fcfs_bwd_tma.cuh"
 
 namespace fcfs {
 namespace {
 
-// span-wide adjoint weight rows of one axis for channel c
-template <int S, int SPAN>
-__device__ __forceinline__ void stage_adj_span(float* WF, const AxisP& A, const AdjP& J, int c) {
-    for (int e = threadIdx.x; e < S * SPAN; e += blockDim.x) {
-        const int u = e / SPAN, k = e - u * SPAN;
-        const int t = k - J.off[u];
+// span-wide adjoint weight rows of one axis for channel c, shifted right by
+// `shift` positions inside rows of W entries (zero outside the taps)
+template <int S, int W>
+__device__ __forceinline__ void stage_adj_span(float* WF, const AxisP& A, const AdjP& J, int c, int shift) {
+    for (int e = threadIdx.x; e < S * W; e += blockDim.x) {
+        const int u = e / W, k = e - u * W;
+        const int t = k - shift - J.off[u];
         float v = 0.f;
         if (t >= 0 && t < J.ntu[u]) {
             const int f = J.idx[u * kMaxAdjTaps + t];
@@ -26,12 +29,52 @@ __device__ __forceinline__ void stage_adj_span(float* WF, const AxisP& A, const 
     }
 }
 
-// XSPEC: one adjoint window per thread in the x pass (lanes stride r samples:
-// bank-conflict free for odd r); otherwise one intermediate column per thread.
-template <int S, int SPAN, typename Tg, typename Tx, bool XSPEC>
-__global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
+// VW consecutive samples of a staged g row as FP32 (VW * sizeof(Tg) = 8 or 16
+// bytes, aligned)
+template <int VW, typename Tg>
+__device__ __forceinline__ void load_vec(const Tg* p, float* v) {
+    if constexpr (std::is_same<Tg, float>::value) {
+        if constexpr (VW == 2) {
+            const float2 t = *reinterpret_cast<const float2*>(p);
+            v[0] = t.x, v[1] = t.y;
+        } else {
+            static_assert(VW == 4, "FP32 vector loads of 2 or 4 samples");
+            const float4 t = *reinterpret_cast<const float4*>(p);
+            v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+        }
+    } else {
+        static_assert(VW == 4 || VW == 8, "BF16 vector loads of 4 or 8 samples");
+        if constexpr (VW == 4) {
+            const uint2 t = *reinterpret_cast<const uint2*>(p);
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.y));
+            v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+        } else {
+            const uint4 t = *reinterpret_cast<const uint4*>(p);
+            const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
+                v[2 * k] = a.x, v[2 * k + 1] = a.y;
+            }
+        }
+    }
+}
+
+// XSPEC: one adjoint window per thread in the x pass (lanes stride r samples).
+// VW = 1: scalar loads (bank-conflict free for odd r or r * sizeof(Tg) <= 4).
+// VW = r (r * sizeof(Tg) = 8 or 16 bytes): a window's samples are read as
+// vectors from the VW-aligned position at or before its first sample, so the
+// lanes' loads are contiguous; the x weight rows are widened to SPANX and
+// shifted by that offset (the same for every window of the launch).
+// Otherwise one intermediate column per thread.  Four CTAs per SM (at most 64
+// registers a thread): the passes are latency-bound between barriers, and the
+// extra resident CTAs measured faster than the larger register budget.
+template <int S, int SPAN, int VW, typename Tg, typename Tx, bool XSPEC>
+__global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
+    constexpr int SPANX = VW > 1 ? (SPAN + 2 * VW - 2) / VW * VW : SPAN;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ float sWFx[S * SPAN], sWFy[S * SPAN];
+    __shared__ float sWFx[S * SPANX], sWFy[S * SPAN];
     const AdjP& JX = T.aj[2];
     const AdjP& JY = T.aj[1];
     float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
@@ -67,7 +110,7 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant
     }
     __syncthreads();
     const bool learn = T.ax[2].learn || T.ax[1].learn;
-    int cur_c = -1;
+    int cur_c = -1, cur_m = 0;
     int stg = 0;
     uint32_t phase = 0;
     for (; tile < tile_end; ++tile) {
@@ -77,11 +120,13 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant
         if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
         __syncthreads();
         const DxGeo geo = sgeo[stg];
-        if (cur_c < 0 || (learn && geo.c != cur_c)) {
+        const int m = geo.xoff & (VW - 1);  // first window's offset from the VW-aligned position
+        if (cur_c < 0 || (learn && geo.c != cur_c) || m != cur_m) {
             // the previous tile ended with a barrier: no thread still reads the weights
-            stage_adj_span<S, SPAN>(sWFx, T.ax[2], JX, geo.c);
-            stage_adj_span<S, SPAN>(sWFy, T.ax[1], JY, geo.c);
+            stage_adj_span<S, SPANX>(sWFx, T.ax[2], JX, geo.c, m);
+            stage_adj_span<S, SPAN>(sWFy, T.ax[1], JY, geo.c, 0);
             cur_c = geo.c;
+            cur_m = m;
             __syncthreads();
         }
 
@@ -93,22 +138,27 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant
         if (g1 < G1) {
             if (XSPEC) {
                 if (xi < nAX) {
-                    float wf[S][SPAN];
+                    float wf[S][SPANX];
 #pragma unroll
                     for (int u = 0; u < S; ++u)
 #pragma unroll
-                        for (int q = 0; q < SPAN; ++q) wf[u][q] = sWFx[u * SPAN + q];
-                    const Tg* src = G0 + g1 * GBW + geo.xoff + xi * R;
+                        for (int q = 0; q < SPANX; ++q) wf[u][q] = sWFx[u * SPANX + q];
+                    const Tg* src = G0 + g1 * GBW + (geo.xoff - m) + xi * R;
                     float* dst = sF + g1 * FXP + xi * S;
                     for (int gr = g1; gr < nGR; gr += G1) {
-                        float v[SPAN];
+                        float v[SPANX];
+                        if constexpr (VW > 1) {
 #pragma unroll
-                        for (int q = 0; q < SPAN; ++q) v[q] = to_f<Tg>(src[q]);
+                            for (int q = 0; q < SPANX; q += VW) load_vec<VW, Tg>(src + q, v + q);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < SPANX; ++q) v[q] = to_f<Tg>(src[q]);
+                        }
 #pragma unroll
                         for (int u = 0; u < S; ++u) {
                             float acc = 0.f;
 #pragma unroll
-                            for (int q = 0; q < SPAN; ++q) acc = fmaf(wf[u][q], v[q], acc);
+                            for (int q = 0; q < SPANX; ++q) acc = fmaf(wf[u][q], v[q], acc);
                             dst[u] = acc;
                         }
                         src += G1 * GBW;
@@ -217,32 +267,35 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant
     }
 }
 
-template <int S, int SPAN, typename Tg>
+template <int S, int SPAN, int VW, typename Tg>
 cudaError_t run_rs(const TmaDxParams& T, cudaStream_t st) {
-    const size_t smem = (size_t)T.bar_off + 8 * T.stages;
+    constexpr int SPANX = VW > 1 ? (SPAN + 2 * VW - 2) / VW * VW : SPAN;
     // measured: the variant pays off when the x pass can own whole windows
-    // (odd r, bank-conflict free) and the weight rows stay small; otherwise
-    // the per-output kernel is faster
-    const bool xs = (T.aj[2].r % 2) == 1;
-    if (!xs || S * SPAN > 40) return cudaErrorInvalidValue;
-    auto k = fcfs_bwd_dx2d_rs<S, SPAN, Tg, Tg, true>;
-    if (T.WAcap > T.threads) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
-    k<<<(unsigned)grid, T.threads, smem, st>>>(T);
-    return cudaGetLastError();
+    // without bank conflicts and the weight rows stay small; otherwise the
+    // per-output kernel is faster (and wider rows are not instantiated)
+    if constexpr (S * SPANX > 40) {
+        return cudaErrorInvalidValue;
+    } else {
+        const size_t smem = (size_t)T.bar_off + 8 * T.stages;
+        auto k = fcfs_bwd_dx2d_rs<S, SPAN, VW, Tg, Tg, true>;
+        if (T.WAcap > T.threads) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
+        k<<<(unsigned)grid, T.threads, smem, st>>>(T);
+        return cudaGetLastError();
+    }
 }
 
 }  // namespace
 
-#define FCFS_DX_RS_PAIRS(X) X(4, 10) X(2, 7) X(2, 4) X(3, 4)
+#define FCFS_DX_RS_PAIRS(X) X(4, 10) X(2, 7) X(2, 4) X(3, 4) X(3, 8)
 
 bool dx_rs_compiled(int S, int span) {
 #define CASE(a, b) \
@@ -252,11 +305,29 @@ bool dx_rs_compiled(int S, int span) {
     return false;
 }
 
+// x-pass vector width for adjoint stride r and element size es: 1 when scalar
+// loads are bank-conflict free, r when a window's samples form 8- or 16-byte
+// vectors, 0 when neither holds
+int dx_rs_vector_width(int r, int es) {
+    if (r % 2 == 1 || r * es <= 4) return 1;
+    if (r * es == 8 || r * es == 16) return r;
+    return 0;
+}
+
 cudaError_t launch_dx_rs(const TmaDxParams& T, int dt, cudaStream_t st) {
-    const int S = T.aj[2].s, span = T.rs_span;
-#define CASE(a, b)                                                                              \
-    if (S == a && span == b)                                                                    \
-        return dt == FCFS_F32 ? run_rs<a, b, float>(T, st) : run_rs<a, b, __nv_bfloat16>(T, st);
+    const int S = T.aj[2].s, span = T.rs_span, vw = T.rs_vw;
+#define CASE(a, b)                                                    \
+    if (S == a && span == b) {                                        \
+        if (dt == FCFS_F32) {                                         \
+            if (vw == 1) return run_rs<a, b, 1, float>(T, st);        \
+            if (vw == 2) return run_rs<a, b, 2, float>(T, st);        \
+            if (vw == 4) return run_rs<a, b, 4, float>(T, st);        \
+        } else {                                                      \
+            if (vw == 1) return run_rs<a, b, 1, __nv_bfloat16>(T, st); \
+            if (vw == 4) return run_rs<a, b, 4, __nv_bfloat16>(T, st); \
+        }                                                             \
+        return cudaErrorInvalidValue;                                 \
+    }
     FCFS_DX_RS_PAIRS(CASE)
 #undef CASE
     return cudaErrorInvalidValue;

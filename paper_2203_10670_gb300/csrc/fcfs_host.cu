@@ -707,9 +707,13 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
         for (int u = 0; u < J.s; ++u) sp = std::max(sp, J.off[u] + J.ntu[u]);
         return sp;
     };
-    const bool rs_ok = T->aj[2].s == T->aj[1].s && T->aj[2].r == T->aj[1].r &&
-                       true_span(T->aj[2]) == true_span(T->aj[1]) && dx_rs_compiled(T->aj[2].s, true_span(T->aj[2]));
+    bool rs_ok = T->aj[2].s == T->aj[1].s && T->aj[2].r == T->aj[1].r &&
+                 true_span(T->aj[2]) == true_span(T->aj[1]) && dx_rs_compiled(T->aj[2].s, true_span(T->aj[2]));
+    T->rs_vw = rs_ok ? dx_rs_vector_width(T->aj[2].r, es) : 0;
+    rs_ok = rs_ok && T->rs_vw > 0;
     T->rs_span = rs_ok ? true_span(T->aj[2]) : 0;
+    // a vector-loading x pass reads up to SPANX samples from the aligned position before each window
+    const int spanx = rs_ok && T->rs_vw > 1 ? (T->rs_span + 2 * T->rs_vw - 2) / T->rs_vw * T->rs_vw : 0;
     for (int it = 0; it < 8; ++it) {
         // capacities over every tile position of each axis
         int vx = 1, vy = 1, gw = 1, gh = 1, wa = 1;
@@ -717,7 +721,7 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
             const AxRange R = ax_range(T->aj[2], d->pad, q0, std::min(Nx, q0 + T->QX) - 1);
             vx = std::max(vx, R.vhi - R.vlo + 1);
             if (R.ahi >= R.alo) {
-                gw = std::max(gw, (R.ahi - R.alo) * T->aj[2].r + T->aj[2].span);
+                gw = std::max(gw, (R.ahi - R.alo) * T->aj[2].r + std::max(T->aj[2].span, spanx));
                 wa = std::max(wa, R.ahi - R.alo + 1);
             }
         }

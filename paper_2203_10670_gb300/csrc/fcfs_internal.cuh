@@ -143,6 +143,7 @@ struct TmaDxParams {
     // register-blocked variant: span every adjoint window reads (same on both
     // axes), adjoint windows per tile row, pitch of the window-relative Fx
     int rs_span, WAcap, FXP;
+    int rs_vw;  // register-blocked x pass: elements per vector load of a window (1 = scalar loads)
 };
 
 // Bulk-copy staged input-gradient parameters (3D): the 2D tile of real
@@ -308,6 +309,7 @@ cudaError_t launch_forward3d_tma(const TmaFwd3Params& T, int nt, int din, int do
 cudaError_t launch_forward3d_rs(const TmaFwd3Params& T, int din, int dout, cudaStream_t st);
 cudaError_t launch_dx3d_tma(const TmaDx3Params& T, int nt, int dt, cudaStream_t st);
 bool dx_rs_compiled(int S, int span);
+int dx_rs_vector_width(int r, int es);
 cudaError_t launch_dw_tma(const TmaDwParams& T, int nt, int dt, cudaStream_t st, const void* x);
 bool dw_rb_compiled(int r, int nt);
 size_t forward_smem_bytes(const FwdParams& P, bool is3d);

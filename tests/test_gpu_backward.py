@@ -76,6 +76,18 @@ def test_dx_fixed_methods(F, orc, ratios, method, pad):
     check_dx(F, orc, (2, 2, 45, 299), [F.Axis(r, s, method) for r, s in ratios], pad, seed=3 + method)
 
 
+@pytest.mark.parametrize("ratio", ((2, 3), (4, 3), (3, 2)))
+@pytest.mark.parametrize("method", (BILINEAR, BICUBIC))
+@pytest.mark.parametrize("pad", (REPL, CONST, REFL))
+@pytest.mark.parametrize("dtype", (torch.float32, torch.bfloat16))
+def test_dx_bulk_copy_same_ratio(F, orc, ratio, method, pad, dtype):
+    # g rows of 16-byte multiples and the same ratio on both axes: the bulk-copy
+    # input gradient, register-blocked where the adjoint span is compiled (x pass
+    # with vector loads for r * sizeof = 8 or 16 bytes); 3 x 11 tiles, ragged
+    W = 300 if ratio != (3, 2) else 304
+    check_dx(F, orc, (2, 2, 263, W), [F.Axis(*ratio, method)] * 2, pad, dtype=dtype, seed=17 + method)
+
+
 @pytest.mark.parametrize("ratio", ((3, 2), (2, 3), (7, 5)))
 @pytest.mark.parametrize("pad", (REPL, REFL))
 def test_dx_1d_and_tiny(F, orc, ratio, pad):
