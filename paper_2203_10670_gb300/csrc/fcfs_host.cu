@@ -744,7 +744,10 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
         T->w_off = T->fx_off + T->GBH * T->FXP * 4;
         T->tab_off = T->w_off + (T->aj[2].s + T->aj[1].s) * w * 4;
         T->bar_off = (T->tab_off + (T->VXcap + T->VYcap) * 4 + 15) / 16 * 16;
-        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 8 * T->stages <= 56 * 1024) break;
+        // the register-blocked kernel runs at most four CTAs per SM (registers) and gains from
+        // taller tiles (less halo per output row); the per-output kernel from more resident CTAs
+        const size_t budget = rs_ok ? 110 * 1024 : 56 * 1024;
+        if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 8 * T->stages <= budget) break;
         if (T->QX > 64 && T->QX >= 4 * T->QY) T->QX /= 2;
         else if (T->QY > 8) T->QY /= 2;
         else if (T->QX > 32) T->QX /= 2;
