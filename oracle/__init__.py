@@ -304,3 +304,39 @@ def weight_grad_full2d(x, g, axes, per_channel, pad=PAD_REPLICATE, pad_value=0.0
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return dw
+
+
+# ------------------------------------------------------- fused epilogue (FCN layer)
+
+ACT_NONE, ACT_RELU, ACT_LEAKY_RELU, ACT_CLAMP = 0, 1, 2, 3
+
+
+def resize_fused(x, axes, mix=None, bias=None, act=ACT_NONE, alpha=0.0, lo=0.0, hi=0.0, pad=PAD_REPLICATE,
+                 pad_value=0.0, align=None):
+    """FCFS followed by the pointwise layer that comes next in a fully convolutional
+    network (Sec. 1: the resize as one layer of an FCN; Sec. 4 for the 2D layer):
+        z = FCFS(x)                                  (the oracle's direct formula)
+        v[n,o,p] = sum_c mix[o][c] z[n,c,p] + bias[o]  (a 1x1 convolution; mix None: v = z)
+        y = act(v): none, relu max(v, 0), leaky relu (v if v >= 0 else alpha v),
+                    clamp min(max(v, lo), hi).
+    Float64 throughout; the channel sum is a library matrix product (one step)."""
+    if align is not None:
+        axes = [dict(a, align=align) for a in axes]
+    z = resize(x, axes, pad=pad, pad_value=pad_value)
+    nd = z.ndim - 2
+    if mix is None:
+        v = z.copy()
+    else:
+        mix = np.asarray(mix, dtype=np.float64)
+        v = np.einsum("oc,nc...->no...", mix, z)
+    if bias is not None:
+        v = v + np.asarray(bias, dtype=np.float64).reshape((1, -1) + (1,) * nd)
+    if act == ACT_RELU:
+        v = np.maximum(v, 0.0)
+    elif act == ACT_LEAKY_RELU:
+        v = np.where(v >= 0.0, v, alpha * v)
+    elif act == ACT_CLAMP:
+        v = np.minimum(np.maximum(v, lo), hi)
+    elif act != ACT_NONE:
+        raise ValueError("unknown activation")
+    return v

@@ -767,3 +767,48 @@ def test_full2d_outer_product_is_the_separable_layer(orc):
     per = orc.weight_grad_full2d(x, g, axes, True, pad=REFL)
     shared = orc.weight_grad_full2d(x, g, axes, False, pad=REFL)
     assert np.abs(per.sum(0) - shared).max() <= 1e-12 * (1 + np.abs(shared).max())
+
+
+# ------------------------------------------------ fused epilogue (FCN layer, f3)
+
+@pytest.mark.parametrize("ratios,method", [([(2, 1), (2, 1)], BILINEAR), ([(4, 3), (2, 3)], BICUBIC),
+                                           ([(3, 2), (3, 2)], NEAREST)])
+@pytest.mark.parametrize("act", (0, 1, 2, 3))
+def test_fused_matches_construction_then_library_conv1x1(orc, ratios, method, act):
+    """The paper's construction (library ops) followed by torch's 1x1 convolution, bias and
+    activation in float64 equals the oracle's fused layer."""
+    import torch
+    import torch.nn.functional as F
+
+    rng = np.random.default_rng(61 + act + 3 * method)
+    C, O = 3, 5
+    x = rng.standard_normal((2, C, 9, 11))
+    mix = rng.standard_normal((O, C))
+    bias = rng.standard_normal(O)
+    axes = []
+    for r, s in ratios:
+        W, K = orc.make_weights(method, r, s, 0)
+        axes.append(dict(r=r, s=s, method=method, K=K, w=W))
+    z = torch.from_numpy(_construction(x, axes, REFL, 0.0))
+    v = F.conv2d(z, torch.from_numpy(mix).reshape(O, C, 1, 1), torch.from_numpy(bias))
+    want = {0: lambda t: t, 1: F.relu, 2: lambda t: F.leaky_relu(t, 0.2),
+            3: lambda t: torch.clamp(t, -0.5, 0.75)}[act](v).numpy()
+    got = orc.resize_fused(x, [dict(r=r, s=s, method=method) for r, s in ratios], mix, bias, act, alpha=0.2,
+                           lo=-0.5, hi=0.75, pad=REFL)
+    assert got.shape == want.shape
+    assert np.abs(got - want).max() <= 1e-12 * (1 + np.abs(want).max())
+
+
+def test_fused_identity_mix_is_the_plain_layer(orc):
+    rng = np.random.default_rng(67)
+    x = rng.standard_normal((1, 4, 10, 12))
+    axes = [dict(r=3, s=2, method=BICUBIC)] * 2
+    z = orc.resize(x, axes, pad=CONST, pad_value=0.25)
+    assert np.array_equal(orc.resize_fused(x, axes, pad=CONST, pad_value=0.25), z)
+    # relu of the identity layer keeps exactly the positive outputs
+    y = orc.resize_fused(x, axes, act=1, pad=CONST, pad_value=0.25)
+    assert np.array_equal(y, np.where(z > 0, z, 0.0))
+    # a mix that permutes channels permutes the outputs
+    perm = np.eye(4)[[2, 0, 3, 1]]
+    assert np.allclose(orc.resize_fused(x, axes, mix=perm, pad=CONST, pad_value=0.25), z[:, [2, 0, 3, 1]],
+                       rtol=0, atol=1e-15)
