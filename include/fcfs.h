@@ -152,6 +152,33 @@ typedef struct {
  */
 int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream);
 
+/* Activation of the fused epilogue. */
+typedef enum { FCFS_ACT_NONE = 0, FCFS_ACT_RELU = 1, FCFS_ACT_LEAKY_RELU = 2, FCFS_ACT_CLAMP = 3 } fcfs_act;
+
+/* The pointwise layer that follows FCFS in a fully convolutional network. */
+typedef struct {
+    int c_out;          /* output channels (>= 1) */
+    const float* mix;   /* DEVICE [c_out][c] FP32 1x1 convolution, or NULL = identity (c_out == c) */
+    const float* bias;  /* DEVICE [c_out] FP32, or NULL */
+    int act;            /* fcfs_act */
+    float alpha;        /* FCFS_ACT_LEAKY_RELU: slope for negative inputs */
+    float lo, hi;       /* FCFS_ACT_CLAMP: bounds (lo <= hi) */
+} fcfs_epilogue;
+
+/*
+ * FCFS fused with the layer after it (Sec. 1: the resize as one layer of an
+ * FCN; Sec. 4 for 2D):
+ *   y[n,o,p] = act(sum_c mix[o][c] FCFS(x)[n,c,p] + bias[o])
+ * relu max(v, 0); leaky relu v >= 0 ? v : alpha v; clamp min(max(v, lo), hi).
+ * The FCFS outputs of all c channels are combined on chip and never written.
+ * d: a 2D separable descriptor (fixed or learnable axes, any pad / align;
+ * w2d must be NULL; r_y r_x <= 512); x: DEVICE [n][c][H][W] of dtype_in;
+ * y: DEVICE [n][c_out][Ho][Wo] of dtype_out, fully overwritten.  FP32
+ * arithmetic.  Errors: as fcfs_forward, FCFS_ERR_ARG for a bad epilogue,
+ * FCFS_ERR_UNSUPPORTED outside the 2D separable layer.  Forward only.
+ */
+int fcfs_forward_fused(const fcfs_desc* d, const fcfs_epilogue* e, const void* x, void* y, void* stream);
+
 /*
  * Bytes of device workspace fcfs_backward needs for the weight gradients
  * requested by the descriptor (0 when no axis has learnable weights).

@@ -26,6 +26,7 @@ FCFS_NEAREST, FCFS_BILINEAR, FCFS_BICUBIC = 0, 1, 2
 FCFS_PAD_REPLICATE, FCFS_PAD_CONSTANT, FCFS_PAD_REFLECT = 0, 1, 2
 # fcfs_align
 FCFS_ALIGN_PAPER, FCFS_ALIGN_HALF_PIXEL, FCFS_ALIGN_FLOOR = 0, 1, 2
+FCFS_ACT_NONE, FCFS_ACT_RELU, FCFS_ACT_LEAKY_RELU, FCFS_ACT_CLAMP = 0, 1, 2, 3
 # fcfs_dtype
 FCFS_F32, FCFS_BF16, FCFS_U8 = 0, 1, 2
 FCFS_MAX_R = 64
@@ -43,6 +44,11 @@ class fcfs_desc(ctypes.Structure):
                 ("dtype_in", ctypes.c_int), ("dtype_out", ctypes.c_int), ("pad", ctypes.c_int),
                 ("pad_value", ctypes.c_float), ("align", ctypes.c_int), ("axis", fcfs_axis * 3),
                 ("cubic_a", ctypes.c_float), ("w2d", ctypes.c_void_p), ("w2d_per_channel", ctypes.c_int)]
+
+
+class fcfs_epilogue(ctypes.Structure):
+    _fields_ = [("c_out", ctypes.c_int), ("mix", ctypes.c_void_p), ("bias", ctypes.c_void_p), ("act", ctypes.c_int),
+                ("alpha", ctypes.c_float), ("lo", ctypes.c_float), ("hi", ctypes.c_float)]
 
 
 class fcfs_serve_config(ctypes.Structure):
@@ -68,6 +74,7 @@ SIGNATURES = {
     "fcfs_make_weights": (_I, [_I, _I, _I, _I, _P, ctypes.POINTER(_I)]),
     "fcfs_geometry": (_I, [_I, _I, _I, _I, _LL, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_I)]),
     "fcfs_forward": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P]),
+    "fcfs_forward_fused": (_I, [ctypes.POINTER(fcfs_desc), ctypes.POINTER(fcfs_epilogue), _P, _P, _P]),
     "fcfs_backward_workspace": (ctypes.c_size_t, [ctypes.POINTER(fcfs_desc)]),
     "fcfs_backward": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "fcfs_status_string": (ctypes.c_char_p, [_I]),

@@ -277,6 +277,49 @@ class FCFS(torch.nn.Module):
         return FCFSFunction.apply(x, spec, *ws)
 
 
+# ------------------------------------------- fused pointwise layer (FCN)
+
+ACT_NONE, ACT_RELU, ACT_LEAKY_RELU, ACT_CLAMP = (N.FCFS_ACT_NONE, N.FCFS_ACT_RELU, N.FCFS_ACT_LEAKY_RELU,
+                                                 N.FCFS_ACT_CLAMP)
+
+
+def fcfs_forward_fused(desc: N.fcfs_desc, epi: N.fcfs_epilogue, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    check(N.load().fcfs_forward_fused(ctypes.byref(desc), ctypes.byref(epi), x_ptr, y_ptr, stream),
+          "fcfs_forward_fused")
+
+
+def resize_fused(x: torch.Tensor, axes: Sequence[Axis], mix: Optional[torch.Tensor] = None,
+                 bias: Optional[torch.Tensor] = None, act: int = ACT_NONE, alpha: float = 0.0, lo: float = 0.0,
+                 hi: float = 0.0, pad: int = PAD_REPLICATE, pad_value: float = 0.0,
+                 out_dtype: Optional[torch.dtype] = None, align: int = ALIGN_PAPER, cubic_a: float = 0.0,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """y = act(mix @ FCFS(x) + bias) over channels, in one kernel (x [n, c, H, W] on a CUDA device;
+    mix [c_out, c] float32 or None for the identity; bias [c_out] or None)."""
+    if out_dtype is None:
+        out_dtype = out.dtype if out is not None else torch.float32 if x.dtype == torch.uint8 else x.dtype
+    x = x.contiguous()
+    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value, align, cubic_a)
+    e = N.fcfs_epilogue()
+    for name, t in (("mix", mix), ("bias", bias)):
+        if t is not None and (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    e.c_out = int(mix.shape[0]) if mix is not None else int(x.shape[1])
+    if mix is not None and tuple(mix.shape) != (e.c_out, x.shape[1]):
+        raise ValueError("mix must be [c_out, c]")
+    if bias is not None and tuple(bias.shape) != (e.c_out,):
+        raise ValueError("bias must be [c_out]")
+    e.mix = mix.data_ptr() if mix is not None else None
+    e.bias = bias.data_ptr() if bias is not None else None
+    e.act, e.alpha, e.lo, e.hi = int(act), float(alpha), float(lo), float(hi)
+    oshape = (x.shape[0], e.c_out) + out_shape(x.shape, axes)[2:]
+    if out is None:
+        out = torch.empty(oshape, dtype=out_dtype, device=x.device)
+    elif tuple(out.shape) != oshape or out.dtype != out_dtype or not out.is_contiguous():
+        raise ValueError("out has the wrong shape, dtype or layout")
+    fcfs_forward_fused(d, e, x.data_ptr(), out.data_ptr(), _stream(x.device))
+    return out
+
+
 # ------------------------------------------------- non-separable 2D kernels
 
 def _full2d_axes(axes: Sequence[Axis], w2d: torch.Tensor):

@@ -192,3 +192,32 @@ def test_nonseparable_descriptor_errors(native):
     # partial-sum records: planes x chunks x (r_y r_x T_y T_x) floats, bilinear 3/2 -> T = 3
     ws = lib.fcfs_backward_workspace(ctypes.byref(d))
     assert ws > 0 and ws % (4 * 9 * 9) == 0
+
+
+def test_fused_epilogue_errors(native):
+    """Validation of fcfs_forward_fused; every case fails on the host before any device work."""
+    lib = native.load()
+    d = _desc(native)
+
+    def run(**kw):
+        e = native.fcfs_epilogue()
+        e.c_out, e.mix = 4, BOGUS
+        for k, v in kw.items():
+            setattr(e, k, v)
+        return lib.fcfs_forward_fused(ctypes.byref(d), ctypes.byref(e), BOGUS, BOGUS, None)
+
+    assert run(c_out=0) == native.FCFS_ERR_ARG
+    assert run(mix=None, c_out=2) == native.FCFS_ERR_ARG  # identity needs c_out == c (= 1)
+    assert run(act=7) == native.FCFS_ERR_ARG
+    assert run(act=native.FCFS_ACT_CLAMP, lo=1.0, hi=0.0) == native.FCFS_ERR_ARG
+    assert run(alpha=float("nan")) == native.FCFS_ERR_ARG
+    assert run(mix=BOGUS + 2) == native.FCFS_ERR_ARG  # misaligned
+    assert lib.fcfs_forward_fused(ctypes.byref(d), None, BOGUS, BOGUS, None) == native.FCFS_ERR_ARG
+    d = _desc(native, w2d=BOGUS)
+    assert run() == native.FCFS_ERR_UNSUPPORTED
+    from paper_2203_10670_gb300 import fcfs
+
+    d = fcfs.make_desc((1, 1, 8, 8), [fcfs.Axis(32, 1, 1), fcfs.Axis(32, 1, 1)], 0, 0)
+    assert run() == native.FCFS_ERR_UNSUPPORTED  # r_y r_x > 512
+    d = fcfs.make_desc((1, 1, 8, 8, 8), [fcfs.Axis(2, 1, 1)] * 3, 0, 0)
+    assert run() == native.FCFS_ERR_UNSUPPORTED  # 3D
