@@ -58,6 +58,9 @@ def parse():
                         "input gradient of that c2 op (fp32), with --batch images")
     p.add_argument("--volume", action="store_true",
                    help="time only the c5 volume (1x1x256^3 fp32, trilinear 3/2): forward and input gradient")
+    p.add_argument("--fused", action="store_true",
+                   help="time only the fused resize + 1x1 conv + ReLU decoder block (8x64x256^2, x2), "
+                        "fused and unfused, in --dtype")
     p.add_argument("--full2d", action="store_true",
                    help="time only the non-separable 5x5 learnable kernels on the c3 tensor (bf16, 5/4), "
                         "with --batch images: forward, input gradient, both gradients")
@@ -407,6 +410,9 @@ def extras(fcfs, inputs, device, stream, peak, tune=True):
     for k, v in full2d_times(fcfs, inputs, device, stream, peak).items():
         out[f"f2_nonseparable_5x5_bf16_{k}"] = v
     torch.cuda.empty_cache()
+    for dt in (torch.float32, torch.bfloat16):
+        out[f"f3_fused_x2_conv1x1_64_relu_{str(dt)[-4:]}"] = fused_times(fcfs, inputs, device, stream, peak, dtype=dt)
+        torch.cuda.empty_cache()
     out.update(serve_bench(fcfs, inputs, device))
     return out
 
@@ -452,6 +458,79 @@ def full2d_times(fcfs, inputs, device, stream, peak, batch=None, steps=5, warmup
         out[key] = {"ms": t * 1e3, "Gpix_s": px / t / 1e9, "hbm_frac": nbytes / t / 1e9 / peak,
                     "alu_frac": nflop / t / 1e12 / FP32_ALU_TFLOPS}
     return out
+
+
+def fused_times(fcfs, inputs, device, stream, peak, batch=None, steps=5, warmup=1, dtype=torch.float32):
+    """A decoder block of a fully convolutional network: 8x64x256^2, bilinear x2 (2/1 both axes), then a
+    1x1 convolution 64 -> 64 with bias and ReLU, in one fused kernel; beside it the same layer unfused
+    (the plain resize, then torch's 1x1 convolution and ReLU) for context."""
+    shape = (batch or 8, 64, 256, 256)
+    ax = [fcfs.Axis(2, 1, fcfs.BILINEAR)] * 2
+    x = inputs.normal(shape, 81, device=device, dtype=dtype)
+    mix = (inputs.normal((64, 64), 82, device=device) / 8).contiguous()
+    b = inputs.normal((64,), 83, device=device)
+    y = fcfs.resize_fused(x, ax, mix, b, fcfs.ACT_RELU)
+
+    def fused():
+        fcfs.resize_fused(x, ax, mix, b, fcfs.ACT_RELU, out=y)
+
+    z = fcfs.resize(x, ax)
+    w4 = mix.to(dtype).view(64, 64, 1, 1)
+    bd = b.to(dtype)
+
+    def unfused():
+        fcfs.resize(x, ax, out=z)
+        torch.relu_(torch.nn.functional.conv2d(z, w4, bd))
+
+    for _ in range(max(1, warmup)):
+        fused(), unfused()
+    tf = timed(fused, steps, stream) / steps
+    tu = timed(unfused, steps, stream) / steps
+    es = x.element_size()
+    px = shape[0] * y.shape[2] * y.shape[3]
+    nbytes = (x.numel() + y.numel()) * es
+    flop = 2.0 * 64 * 64 * px + 2.0 * 2 * 2 * x.shape[1] * px  # mix, plus two 2-tap passes per channel
+    out = {"ms": tf * 1e3, "Gpix_s": px / tf / 1e9, "hbm_frac": nbytes / tf / 1e9 / peak,
+           "alu_frac": flop / tf / 1e12 / FP32_ALU_TFLOPS, "unfused_ms": tu * 1e3}
+    del x, y, z
+    # the epilogue alone: the c2 images (16x3x1080x1920), bicubic 4/3, clamped to [0, 1] on store,
+    # against the plain resize followed by an in-place clamp (one more pass over the output)
+    xs = inputs.uniform(inputs.C2["shape"], inputs.C2["seed"], device=device, dtype=dtype)
+    a2 = [fcfs.Axis(4, 3, fcfs.BICUBIC)] * 2
+    ys = fcfs.resize_fused(xs, a2, act=fcfs.ACT_CLAMP, lo=0.0, hi=1.0)
+    zs = fcfs.resize(xs, a2)
+
+    def fused_clamp():
+        fcfs.resize_fused(xs, a2, act=fcfs.ACT_CLAMP, lo=0.0, hi=1.0, out=ys)
+
+    def plain_clamp():
+        fcfs.resize(xs, a2, out=zs)
+        zs.clamp_(0.0, 1.0)
+
+    for _ in range(max(1, warmup)):
+        fused_clamp(), plain_clamp()
+    tc = timed(fused_clamp, steps, stream) / steps
+    tp = timed(plain_clamp, steps, stream) / steps
+    pxs = ys.shape[0] * ys.shape[2] * ys.shape[3]
+    out["clamp_c2_bicubic_4_3"] = {"ms": tc * 1e3, "Gpix_s": pxs / tc / 1e9,
+                                   "hbm_frac": (xs.numel() + ys.numel()) * es / tc / 1e9 / peak,
+                                   "unfused_ms": tp * 1e3}
+    return out
+
+
+def fused_only(args, device):
+    from paper_2203_10670_gb300 import build as B
+
+    B.build()
+    from paper_2203_10670_gb300 import fcfs, inputs
+
+    stream = torch.cuda.current_stream(device)
+    peak, _ = peaks()
+    dt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    r = fused_times(fcfs, inputs, device, stream, peak, batch=args.batch if args.batch != 16 else None,
+                    steps=args.steps, warmup=args.warmup, dtype=dt)
+    print(json.dumps({"mode": f"fused bilinear x2 + 1x1 conv 64->64 + ReLU, 8x64x256^2 {args.dtype}", **r}),
+          flush=True)
 
 
 def full2d_only(args, device):
@@ -596,6 +675,9 @@ def main():
             return
         if args.full2d:
             full2d_only(args, device)
+            return
+        if args.fused:
+            fused_only(args, device)
             return
         run_ours(args, rank, world, device)
     finally:

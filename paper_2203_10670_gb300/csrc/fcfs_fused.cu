@@ -3,13 +3,17 @@
 // the 2D layer):
 //   y[n,o,p] = act(sum_c M[o][c] FCFS(x)[n,c,p] + b[o])
 //   K10 fcfs_fused2d - a CTA owns one output tile of one image and a block of
-//       OB output channels.  For every input channel it stages the padded
-//       input tile, runs the x and y taps of the gather-staged forward into a
-//       shared-memory FP32 tile z_c, and adds M[o][c] z_c into per-thread
-//       accumulators (PIX pixels x OB output channels, the mix coefficients
-//       read as shared-memory broadcasts).  Bias, activation and the store
-//       follow the last input channel: the C intermediate planes never reach
-//       HBM.  Without a mix (identity) the block is one channel.
+//       OB output channels.  In passes of up to eight input channels it stages
+//       the padded input tiles, runs the x and y taps of the gather-staged
+//       forward into shared-memory FP32 tiles z_c, and adds M[o][c] z_c into
+//       per-thread accumulators (PIX pixels x OB output channels, the mix
+//       coefficients read as float4 shared-memory broadcasts); four barriers
+//       per pass.  Bias, activation and the store follow the last pass: the C
+//       intermediate planes never reach HBM.
+// Without a mix the bias and activation are applied by the store of the
+// planned 2D forward kernels (bulk-copy, register-blocked or gather-staged);
+// only nearest on both axes through the gather kernel comes here, one channel
+// per block.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -34,6 +38,7 @@ struct FusedParams {
     int act;
     float alpha, lo, hi;
     int dtype_out;
+    int kc;            // input channels staged per pass (one barrier triple per pass)
     void* y;
 };
 
@@ -60,14 +65,22 @@ __global__ void __launch_bounds__(kFusedThreads) fcfs_fused2d(const __grid_const
     const int o0 = obk * F.ob, nob = min(F.ob, F.c_out - o0);
     const bool identity = F.mix == nullptr;
     const int c_begin = identity ? o0 : 0, c_end = identity ? o0 + 1 : P.C;
+    const bool learn = AX.learn || AY.learn;
+    const int KC = F.kc;  // input channels per pass
 
+    // per channel of a pass: x and y weights (learnable: one set per channel), input tile,
+    // x-interpolated rows, z tile; then the mix coefficients [c - c_begin][OB]
     const int OX = P.OX, OY = P.OY, pix = OX * OY;
+    const int wxn = AX.r * NT, wyn = AY.r * NT;
+    const int inn = P.IR * P.ICp, hn = P.IR * OX;
+    const int nws = learn ? KC : 1;
     float* sWx = smem;
-    float* sWy = sWx + AX.r * NT;
-    float* sIn = sWy + AY.r * NT;
-    float* sH = sIn + P.IR * P.ICp;
-    float* sZ = sH + P.IR * OX;
-    float* sM = sZ + pix;  // [c - c_begin][OB]
+    float* sWy = sWx + nws * wxn;
+    float* sIn = sWy + nws * wyn;
+    float* sH = sIn + KC * inn;
+    float* sZ = sH + KC * hn;
+    // mix coefficients on a 16-byte boundary: read as float4
+    float* sM = smem + (((sZ + KC * pix) - smem + 3) & ~3);
 
     const int ix0 = tx * P.WX, iy0 = ty * P.WY;
     const int nwx = min(P.WX, AX.n_win - ix0), nwy = min(P.WY, AY.n_win - iy0);
@@ -80,7 +93,6 @@ __global__ void __launch_bounds__(kFusedThreads) fcfs_fused2d(const __grid_const
         if (o < nob) m = identity ? 1.f : __ldg(F.mix + (long long)(o0 + o) * P.C + c_begin + cl);
         sM[k] = m;
     }
-    const bool learn = AX.learn || AY.learn;
     if (!learn) {
         stage_weights<NT>(sWx, AX, 0);
         stage_weights<NT>(sWy, AY, 0);
@@ -94,43 +106,64 @@ __global__ void __launch_bounds__(kFusedThreads) fcfs_fused2d(const __grid_const
 
     const int ox = threadIdx.x % OX, g = threadIdx.x / OX, G = P.G;
     const bool ycol = g < G && ox / AX.r < nwx;
-    for (int c = c_begin; c < c_end; ++c) {
-        if (learn) {
-            // every thread has passed the barrier after the previous pass y, so no one reads the weights
-            stage_weights<NT>(sWx, AX, c);
-            stage_weights<NT>(sWy, AY, c);
+    for (int cb = c_begin; cb < c_end; cb += KC) {
+        const int kn = min(KC, c_end - cb);
+        // the barrier that ended the previous pass's mix frees every buffer of this pass
+        for (int kc = 0; kc < kn; ++kc) {
+            if (learn) {
+                stage_weights<NT>(sWx + kc * wxn, AX, cb + kc);
+                stage_weights<NT>(sWy + kc * wyn, AY, cb + kc);
+            }
+            const long long plane = n * P.C + cb + kc;
+            const Tin* xp = static_cast<const Tin*>(P.x) + plane * (long long)AY.n_in * AX.n_in;
+            load_tile<Tin>(sIn + kc * inn, P.ICp, xp, AY.n_in, AX.n_in, row0, col0, rows, cols, P.pad, P.padv);
         }
-        const long long plane = n * P.C + c;
-        const Tin* xp = static_cast<const Tin*>(P.x) + plane * (long long)AY.n_in * AX.n_in;
-        load_tile<Tin>(sIn, P.ICp, xp, AY.n_in, AX.n_in, row0, col0, rows, cols, P.pad, P.padv);
         __syncthreads();
-        pass_x<NT>(sH, sIn, sWx, AX, OX, P.ICp, rows, nwx, G);
+        for (int kc = 0; kc < kn; ++kc)
+            pass_x<NT>(sH + kc * hn, sIn + kc * inn, sWx + (learn ? kc * wxn : 0), AX, OX, P.ICp, rows, nwx, G);
         __syncthreads();
-        // y taps into the tile z_c (every phase of every window of the tile)
+        // y taps into the z tiles (every phase of every window of the tile)
         if (ycol) {
-            for (int iyl = g; iyl < nwy; iyl += G) {
-                for (int jy = 0; jy < AY.r; ++jy) {
-                    const float* col = sH + (iyl * AY.s + AY.off[jy]) * OX + ox;
-                    const float* wy = sWy + jy * NT;
-                    float a = 0.f;
+            for (int kc = 0; kc < kn; ++kc) {
+                const float* h = sH + kc * hn;
+                const float* wyb = sWy + (learn ? kc * wyn : 0);
+                float* z = sZ + kc * pix;
+                for (int iyl = g; iyl < nwy; iyl += G) {
+                    for (int jy = 0; jy < AY.r; ++jy) {
+                        const float* col = h + (iyl * AY.s + AY.off[jy]) * OX + ox;
+                        const float* wy = wyb + jy * NT;
+                        float a = 0.f;
 #pragma unroll
-                    for (int k = 0; k < NT; ++k) a = fmaf(wy[k], col[k * OX], a);
-                    sZ[(iyl * AY.r + jy) * OX + ox] = a;
+                        for (int k = 0; k < NT; ++k) a = fmaf(wy[k], col[k * OX], a);
+                        z[(iyl * AY.r + jy) * OX + ox] = a;
+                    }
                 }
             }
         }
         __syncthreads();
         // 1x1 mix: acc[p][o] += M[o][c] z_c[p]
-        const float* m = sM + (c - c_begin) * OB;
+        for (int kc = 0; kc < kn; ++kc) {
+            const float4* m4 = reinterpret_cast<const float4*>(sM + (cb + kc - c_begin) * OB);
+            const float* z = sZ + kc * pix;
+            float zv[kFusedPix];
 #pragma unroll
-        for (int k = 0; k < kFusedPix; ++k) {
-            const int p = threadIdx.x + k * kFusedThreads;
-            if (p < pix) {
-                const float z = sZ[p];
+            for (int k = 0; k < kFusedPix; ++k) {
+                const int p = threadIdx.x + k * kFusedThreads;
+                zv[k] = p < pix ? z[p] : 0.f;
+            }
 #pragma unroll
-                for (int o = 0; o < OB; ++o) acc[k][o] = fmaf(m[o], z, acc[k][o]);
+            for (int q = 0; q < OB / 4; ++q) {
+                const float4 mv = m4[q];
+#pragma unroll
+                for (int k = 0; k < kFusedPix; ++k) {
+                    acc[k][4 * q] = fmaf(mv.x, zv[k], acc[k][4 * q]);
+                    acc[k][4 * q + 1] = fmaf(mv.y, zv[k], acc[k][4 * q + 1]);
+                    acc[k][4 * q + 2] = fmaf(mv.z, zv[k], acc[k][4 * q + 2]);
+                    acc[k][4 * q + 3] = fmaf(mv.w, zv[k], acc[k][4 * q + 3]);
+                }
             }
         }
+        __syncthreads();  // the next pass overwrites the z tiles
     }
 
     // bias, activation, store at y[n][o0 + o][oy][ox]
@@ -212,6 +245,11 @@ extern "C" int fcfs_forward_fused(const fcfs_desc* d, const fcfs_epilogue* e, co
     if (((uintptr_t)x) % dtype_size(d->dtype_in) || ((uintptr_t)y) % dtype_size(d->dtype_out))
         return fail(FCFS_ERR_ARG, "x or y not aligned to its element size");
 
+    if (!e->mix && forward_has_epilogue_path(d, x)) {
+        // bias and activation only: the planned forward applies them on its store
+        Epi epi{e->bias, e->act, e->alpha, e->lo, e->hi};
+        return forward_planned(d, x, y, &epi, (cudaStream_t)stream);
+    }
     FusedParams F;
     memset(&F, 0, sizeof F);
     int ntk;
@@ -239,8 +277,16 @@ extern "C" int fcfs_forward_fused(const fcfs_desc* d, const fcfs_epilogue* e, co
     const long long blocks = (long long)F.P.tiles_x * F.P.tiles_y * F.oblocks * d->n;
     if (blocks > INT_MAX) return fail(FCFS_ERR_UNSUPPORTED, "grid too large");
     const long long crange = e->mix ? d->c : 1;
-    const size_t smem = sizeof(float) * ((size_t)(rx + ry) * ntk + (size_t)F.P.IR * F.P.ICp +
-                                         (size_t)F.P.IR * F.P.OX + (size_t)F.P.OX * F.P.OY + (size_t)crange * OB);
+    const bool learn = d->axis[0].w || d->axis[1].w;
+    auto smem_for = [&](int kc) {
+        const size_t per = (size_t)F.P.IR * F.P.ICp + (size_t)F.P.IR * F.P.OX + (size_t)F.P.OX * F.P.OY;
+        return sizeof(float) * ((size_t)(learn ? kc : 1) * (rx + ry) * ntk + (size_t)kc * per + 3 +
+                                (size_t)crange * OB);
+    };
+    // up to 8 input channels per pass while the footprint stays near 48 KB
+    F.kc = (int)std::max(1LL, std::min<long long>(8, crange));
+    while (F.kc > 1 && smem_for(F.kc) > 48 * 1024) --F.kc;
+    const size_t smem = smem_for(F.kc);
     if (smem > 200 * 1024) return fail(FCFS_ERR_UNSUPPORTED, "fused tile needs %zu bytes of shared memory", smem);
     cudaError_t ce = OB == 8 ? launch_fused_ob<8>(F, ntk, d->dtype_in, blocks, smem, (cudaStream_t)stream)
                              : launch_fused_ob<32>(F, ntk, d->dtype_in, blocks, smem, (cudaStream_t)stream);

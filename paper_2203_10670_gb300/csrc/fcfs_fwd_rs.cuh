@@ -182,6 +182,10 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ Tma
                     for (int q = 0; q < SPAN; ++q)
 #pragma unroll
                         for (int c = 0; c < VW; ++c) acc[c] = fmaf(wf[j][q], v[q][c], acc[c]);
+                    if (epi_on(P.epi)) {
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) acc[c] = epi_apply(P.epi, geo.c, acc[c]);
+                    }
                     storev(ybase + (oy0 + j) * AX.n_out, acc, nvalid);
                 }
             }

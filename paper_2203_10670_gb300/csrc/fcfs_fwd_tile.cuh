@@ -118,7 +118,7 @@ __device__ __forceinline__ void fwd2d_tile(const FwdParams& P, long long tile, f
             float acc = 0.f;
 #pragma unroll
             for (int k = 0; k < NT; ++k) acc = fmaf(wy[k], col[k * OX], acc);
-            store_f(yp + (long long)(oyb + jy) * AX.n_out, acc);
+            store_f(yp + (long long)(oyb + jy) * AX.n_out, epi_on(P.epi) ? epi_apply(P.epi, c, acc) : acc);
         }
     }
 }

@@ -305,6 +305,10 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ Tm
 #pragma unroll
                         for (int v = 0; v < VW; ++v) acc[v] = fmaf(w[t], h[v], acc[v]);
                     }
+                    if (epi_on(P.epi)) {
+#pragma unroll
+                        for (int v = 0; v < VW; ++v) acc[v] = epi_apply(P.epi, geo.c, acc[v]);
+                    }
                     storev(ybase + yoff, acc, nvalid);
                     hp += hstep;
                     yoff += ystep;

@@ -440,10 +440,21 @@ int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
         return e == cudaSuccess ? FCFS_OK : cuda_fail(e, "nearest launch");
     }
 
+    return forward_planned(d, x, y, nullptr, st);
+}
+
+}  // extern "C"
+
+namespace fcfs {
+
+// The planned separable forward (bulk-copy or gather kernels, planner cache),
+// with an optional store epilogue (2D only).
+int forward_planned(const fcfs_desc* d, const void* x, void* y, const Epi* epi, cudaStream_t st) {
     FwdParams P;
     int ntk;
-    rc = build_forward_params(d, x, y, &P, &ntk);
+    int rc = build_forward_params(d, x, y, &P, &ntk);
     if (rc) return rc;
+    if (epi) P.epi = *epi;
     TileChoice tc;
     const bool have = get_plan(P, d->ndim, d->dtype_in, d->dtype_out, &tc);
     if (!have) {
@@ -454,9 +465,14 @@ int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
     return launch_choice(d, P, ntk, tc, st);
 }
 
-}  // extern "C"
-
-namespace fcfs {
+// Whether the planned 2D forward of d runs a kernel that applies the store
+// epilogue: every 2D path except the gather kernel for nearest on both axes.
+bool forward_has_epilogue_path(const fcfs_desc* d, const void* x) {
+    if (d->ndim != 2) return false;
+    bool all_nearest = true;
+    for (int a = 0; a < d->ndim; ++a) all_nearest &= (d->axis[a].w == nullptr && d->axis[a].method == FCFS_NEAREST);
+    return !all_nearest || tma_eligible(d, x);
+}
 
 int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* out, int* ntk) {
     int nt = 1;

@@ -49,6 +49,8 @@ void set_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice t);
 void clear_plans();
 bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t);
 int launch_planned(FwdParams& P, int ntk, bool is3d, int din, int dout, cudaStream_t st);
+int forward_planned(const fcfs_desc* d, const void* x, void* y, const Epi* epi, cudaStream_t st);
+bool forward_has_epilogue_path(const fcfs_desc* d, const void* x);
 int build_adjoint(const AxisP& A, AdjAxis* J);
 
 // non-separable 2D kernels (fcfs_full2d.cu)

@@ -33,6 +33,25 @@ struct AxisP {
     float wf[kMaxR * kMaxFixedTaps];  // fixed-method table [r][nt_src]
 };
 
+// Pointwise epilogue of the forward store (the bias and activation of the
+// layer that follows FCFS in a fully convolutional network): act and bias
+// zero for none.
+struct Epi {
+    const float* bias;  // [C] or NULL
+    int act;            // fcfs_act
+    float alpha, lo, hi;
+};
+
+__device__ __forceinline__ bool epi_on(const Epi& e) { return e.act != 0 || e.bias != nullptr; }
+
+__device__ __forceinline__ float epi_apply(const Epi& e, int c, float v) {
+    if (e.bias) v += e.bias[c];
+    if (e.act == FCFS_ACT_RELU) return fmaxf(v, 0.f);
+    if (e.act == FCFS_ACT_LEAKY_RELU) return v >= 0.f ? v : e.alpha * v;
+    if (e.act == FCFS_ACT_CLAMP) return fminf(fmaxf(v, e.lo), e.hi);
+    return v;
+}
+
 // Forward launch parameters.  Axis 0 = D, 1 = H (y), 2 = W (x); missing axes
 // are identity axes of extent 1.
 struct FwdParams {
@@ -50,6 +69,7 @@ struct FwdParams {
     int ring;          // 3D: depth planes kept in shared memory
     const void* x;
     void* y;
+    Epi epi;           // 2D kernels: applied to every output before its store
 };
 
 // Adjoint (transposed) polyphase table of one axis.  With v an extended
