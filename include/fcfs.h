@@ -210,7 +210,9 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
  * Status word written by the device code: 0 when every bounded wait of the
  * bulk-copy kernels completed, else a bit set (1 = a wait on a copy ran past
  * its iteration limit; the kernel finished without hanging but its output is
- * not trustworthy).  Synchronizes the device.  clear != 0 resets the word.
+ * not trustworthy; 4 = an input-gradient tile broke the vector alignment its
+ * plan assumed, output not trustworthy).  Synchronizes the device.  clear != 0
+ * resets the word.
  * Returns the word, or FCFS_ERR_CUDA if it could not be read.
  */
 int fcfs_device_status(int clear);

@@ -64,15 +64,16 @@ __device__ __forceinline__ void load_vec(const Tg* p, float* v) {
 // XSPEC: one adjoint window per thread in the x pass (lanes stride r samples).
 // VW = 1: scalar loads (bank-conflict free for odd r or r * sizeof(Tg) <= 4).
 // VW = r (r * sizeof(Tg) = 8 or 16 bytes): a window's samples are read as
-// vectors from the VW-aligned position at or before its first sample, so the
-// lanes' loads are contiguous; the x weight rows are widened to SPANX and
-// shifted by that offset (the same for every window of the launch).
+// VW-aligned vectors, so the lanes' loads are contiguous; the planner takes
+// this path only when every window starts on a VW boundary of the staged row
+// (the adjoint's first g offset a multiple of r), and the x weight rows are
+// the span rounded up to VW.
 // Otherwise one intermediate column per thread.  Four CTAs per SM (at most 64
 // registers a thread): the passes are latency-bound between barriers, and the
 // extra resident CTAs measured faster than the larger register budget.
 template <int S, int SPAN, int VW, typename Tg, typename Tx, bool XSPEC>
 __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
-    constexpr int SPANX = VW > 1 ? (SPAN + 2 * VW - 2) / VW * VW : SPAN;
+    constexpr int SPANX = (SPAN + VW - 1) / VW * VW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ float sWFx[S * SPANX], sWFy[S * SPAN];
     const AdjP& JX = T.aj[2];
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
     }
     __syncthreads();
     const bool learn = T.ax[2].learn || T.ax[1].learn;
-    int cur_c = -1, cur_m = 0;
+    int cur_c = -1;
     int stg = 0;
     uint32_t phase = 0;
     for (; tile < tile_end; ++tile) {
@@ -120,14 +121,16 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
         if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
         __syncthreads();
         const DxGeo geo = sgeo[stg];
-        const int m = geo.xoff & (VW - 1);  // first window's offset from the VW-aligned position
-        if (cur_c < 0 || (learn && geo.c != cur_c) || m != cur_m) {
+        if (cur_c < 0 || (learn && geo.c != cur_c)) {
             // the previous tile ended with a barrier: no thread still reads the weights
-            stage_adj_span<S, SPANX>(sWFx, T.ax[2], JX, geo.c, m);
+            stage_adj_span<S, SPANX>(sWFx, T.ax[2], JX, geo.c, 0);
             stage_adj_span<S, SPAN>(sWFy, T.ax[1], JY, geo.c, 0);
             cur_c = geo.c;
-            cur_m = m;
             __syncthreads();
+        }
+        // windows start on VW boundaries (planner); a violation is reported, not read past
+        if (VW > 1 && (geo.xoff & (VW - 1)) != 0) {
+            if (threadIdx.x == 0) atomicOr(&g_status_bwd_tma, 4);
         }
 
         const int nAX = geo.X.ahi >= geo.X.alo ? geo.X.ahi - geo.X.alo + 1 : 0;
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
                     for (int u = 0; u < S; ++u)
 #pragma unroll
                         for (int q = 0; q < SPANX; ++q) wf[u][q] = sWFx[u * SPANX + q];
-                    const Tg* src = G0 + g1 * GBW + (geo.xoff - m) + xi * R;
+                    const Tg* src = G0 + g1 * GBW + (geo.xoff & ~(VW - 1)) + xi * R;
                     float* dst = sF + g1 * FXP + xi * S;
                     for (int gr = g1; gr < nGR; gr += G1) {
                         float v[SPANX];
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
 
 template <int S, int SPAN, int VW, typename Tg>
 cudaError_t run_rs(const TmaDxParams& T, cudaStream_t st) {
-    constexpr int SPANX = VW > 1 ? (SPAN + 2 * VW - 2) / VW * VW : SPAN;
+    constexpr int SPANX = (SPAN + VW - 1) / VW * VW;
     // measured: the variant pays off when the x pass can own whole windows
     // without bank conflicts and the weight rows stay small; otherwise the
     // per-output kernel is faster (and wider rows are not instantiated)

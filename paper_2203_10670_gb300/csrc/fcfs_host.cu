@@ -726,10 +726,13 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
     bool rs_ok = T->aj[2].s == T->aj[1].s && T->aj[2].r == T->aj[1].r &&
                  true_span(T->aj[2]) == true_span(T->aj[1]) && dx_rs_compiled(T->aj[2].s, true_span(T->aj[2]));
     T->rs_vw = rs_ok ? dx_rs_vector_width(T->aj[2].r, es) : 0;
+    // vector loads need every adjoint window to start on a VW boundary of the staged row: the
+    // window starts are a r + lo_in with r = VW and the row starts on a 16-byte boundary
+    if (T->rs_vw > 1 && ((T->aj[2].lo_in % T->rs_vw) + T->rs_vw) % T->rs_vw != 0) T->rs_vw = 0;
     rs_ok = rs_ok && T->rs_vw > 0;
     T->rs_span = rs_ok ? true_span(T->aj[2]) : 0;
-    // a vector-loading x pass reads up to SPANX samples from the aligned position before each window
-    const int spanx = rs_ok && T->rs_vw > 1 ? (T->rs_span + 2 * T->rs_vw - 2) / T->rs_vw * T->rs_vw : 0;
+    // a vector-loading x pass reads the span rounded up to VW samples from each window start
+    const int spanx = rs_ok && T->rs_vw > 1 ? (T->rs_span + T->rs_vw - 1) / T->rs_vw * T->rs_vw : 0;
     for (int it = 0; it < 8; ++it) {
         // capacities over every tile position of each axis
         int vx = 1, vy = 1, gw = 1, gh = 1, wa = 1;

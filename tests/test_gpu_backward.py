@@ -57,6 +57,7 @@ def check_dx(F, orc, x_shape, axes, pad, dtype=torch.float32, seed=0):
     gy = inputs.normal(g_shape, seed, dtype=dtype)
     gx, _ = F.resize_backward(None, gy.cuda(), axes, pad, in_shape=x_shape, in_dtype=dtype, need_dx=True)
     torch.cuda.synchronize()
+    assert F.fcfs_device_status(clear=True) == 0  # no bounded wait ran out, no plan invariant broken
     want = orc.adjoint_dx(gy.double().numpy(), x_shape[2:], _oaxes(axes), pad=pad)
     got = gx.double().cpu().numpy()
     scale = float(np.abs(gy.double().numpy()).max()) if gy.numel() else 1.0
