@@ -29,38 +29,6 @@ __device__ __forceinline__ void stage_adj_span(float* WF, const AxisP& A, const 
     }
 }
 
-// VW consecutive samples of a staged g row as FP32 (VW * sizeof(Tg) = 8 or 16
-// bytes, aligned)
-template <int VW, typename Tg>
-__device__ __forceinline__ void load_vec(const Tg* p, float* v) {
-    if constexpr (std::is_same<Tg, float>::value) {
-        if constexpr (VW == 2) {
-            const float2 t = *reinterpret_cast<const float2*>(p);
-            v[0] = t.x, v[1] = t.y;
-        } else {
-            static_assert(VW == 4, "FP32 vector loads of 2 or 4 samples");
-            const float4 t = *reinterpret_cast<const float4*>(p);
-            v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-        }
-    } else {
-        static_assert(VW == 4 || VW == 8, "BF16 vector loads of 4 or 8 samples");
-        if constexpr (VW == 4) {
-            const uint2 t = *reinterpret_cast<const uint2*>(p);
-            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.x));
-            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.y));
-            v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
-        } else {
-            const uint4 t = *reinterpret_cast<const uint4*>(p);
-            const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
-                v[2 * k] = a.x, v[2 * k + 1] = a.y;
-            }
-        }
-    }
-}
-
 // XSPEC: one adjoint window per thread in the x pass (lanes stride r samples).
 // VW = 1: scalar loads (bank-conflict free for odd r or r * sizeof(Tg) <= 4).
 // VW = r (r * sizeof(Tg) = 8 or 16 bytes): a window's samples are read as

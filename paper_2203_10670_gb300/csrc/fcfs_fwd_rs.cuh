@@ -45,8 +45,11 @@ __device__ __forceinline__ void sts_row(float* p, const float* h) {
 
 // XSPEC: window-per-thread x pass (lanes stride s_x samples: bank-conflict
 // free for odd s_x, two-way when s_x samples span 8 bytes); otherwise one
-// output column per thread.
-template <int R, int SPAN, typename Tin, typename Tout, int VW, bool XSPEC>
+// output column per thread.  XV: the s_x samples of a stride span exactly 8
+// bytes and every window starts on such a boundary, so a window is read as
+// 8-byte vectors (the lanes' loads contiguous, no conflicts) and only its
+// SPAN samples enter the sums.
+template <int R, int SPAN, typename Tin, typename Tout, int VW, bool XSPEC, bool XV>
 __global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ TmaFwdParams T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ TileGeo sgeo[2];
@@ -118,9 +121,16 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ Tma
                     const Tin* src = buf + g1 * BW + geo.xoff + xi * SX;
                     float* dst = sH + g1 * OX + xi * R;
                     for (int ry = g1; ry < geo.rows; ry += G1) {
-                        float v[SPAN];
+                        constexpr int VX = 8 / (int)sizeof(Tin);
+                        constexpr int SPANL = XV ? (SPAN + VX - 1) / VX * VX : SPAN;
+                        float v[SPANL];
+                        if constexpr (XV) {
 #pragma unroll
-                        for (int q = 0; q < SPAN; ++q) v[q] = to_f<Tin>(src[q]);
+                            for (int q = 0; q < SPANL; q += VX) load_vec<VX, Tin>(src + q, v + q);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < SPAN; ++q) v[q] = to_f<Tin>(src[q]);
+                        }
                         float h[R];
 #pragma unroll
                         for (int j = 0; j < R; ++j) {
@@ -207,8 +217,14 @@ cudaError_t run_rs(const TmaFwdParams& T, cudaStream_t st) {
     // banks at most two ways: odd s_x, or s_x samples within 8 bytes
     const int sx = T.P.ax[2].s;
     const bool xs = (sx % 2 == 1 || sx * (int)sizeof(Tin) <= 8) && T.P.WX <= (int)T.threads;
-    auto k = v4 ? (xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, true> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, false>)
-                : (xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, true> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, false>);
+    // 8-byte vector window loads: the stride spans 8 bytes and every window starts on a multiple of
+    // s_x samples of the (16-byte aligned) staged row, i.e. lo is a multiple of s_x
+    const int lo = T.P.ax[2].lo;
+    const bool xv = xs && sx * (int)sizeof(Tin) == 8 && ((lo % sx) + sx) % sx == 0;
+    auto k = v4 ? (xv ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, true, true>
+                      : xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, true, false> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, false, false>)
+                : (xv ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, true, true>
+                      : xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, true, false> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, false, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include <cuda.h>
 
 #include "fcfs.h"
@@ -247,6 +249,38 @@ __device__ __forceinline__ float load_f(const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p)));
 }
 __device__ __forceinline__ float load_f(const uint8_t* p) { return (float)__ldg(p); }
+
+// VW consecutive staged samples as FP32 (VW * sizeof(Tg) = 8 or 16 bytes,
+// aligned to that size)
+template <int VW, typename Tg>
+__device__ __forceinline__ void load_vec(const Tg* p, float* v) {
+    if constexpr (std::is_same<Tg, float>::value) {
+        if constexpr (VW == 2) {
+            const float2 t = *reinterpret_cast<const float2*>(p);
+            v[0] = t.x, v[1] = t.y;
+        } else {
+            static_assert(VW == 4, "FP32 vector loads of 2 or 4 samples");
+            const float4 t = *reinterpret_cast<const float4*>(p);
+            v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+        }
+    } else {
+        static_assert(VW == 4 || VW == 8, "BF16 vector loads of 4 or 8 samples");
+        if constexpr (VW == 4) {
+            const uint2 t = *reinterpret_cast<const uint2*>(p);
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&t.y));
+            v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+        } else {
+            const uint4 t = *reinterpret_cast<const uint4*>(p);
+            const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
+                v[2 * k] = a.x, v[2 * k + 1] = a.y;
+            }
+        }
+    }
+}
 
 __device__ __forceinline__ void store_f(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store_f(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
