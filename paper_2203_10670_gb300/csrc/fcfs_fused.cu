@@ -250,6 +250,10 @@ extern "C" int fcfs_forward_fused(const fcfs_desc* d, const fcfs_epilogue* e, co
         Epi epi{e->bias, e->act, e->alpha, e->lo, e->hi};
         return forward_planned(d, x, y, &epi, (cudaStream_t)stream);
     }
+    // a mix of up to 96 input channels: the tensor-core kernel
+    rc = fused_forward_tc(d, e, x, y, (cudaStream_t)stream);
+    if (rc != FCFS_ERR_UNSUPPORTED) return rc;
+    clear_error();
     FusedParams F;
     memset(&F, 0, sizeof F);
     int ntk;

@@ -354,9 +354,9 @@ int fcfs_device_status(int clear) {
     clear_error();
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
-    const int v = read_status_fwd_tma(clear), w = read_status_bwd_tma(clear);
-    if (v < 0 || w < 0) return fail(FCFS_ERR_CUDA, "reading the device status word failed");
-    return v | w;
+    const int v = read_status_fwd_tma(clear), w = read_status_bwd_tma(clear), u = read_status_fused_tc(clear);
+    if (v < 0 || w < 0 || u < 0) return fail(FCFS_ERR_CUDA, "reading the device status word failed");
+    return v | w | u;
 }
 
 int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out) {

@@ -51,6 +51,8 @@ bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t);
 int launch_planned(FwdParams& P, int ntk, bool is3d, int din, int dout, cudaStream_t st);
 int forward_planned(const fcfs_desc* d, const void* x, void* y, const Epi* epi, cudaStream_t st);
 bool forward_has_epilogue_path(const fcfs_desc* d, const void* x);
+int fused_forward_tc(const fcfs_desc* d, const fcfs_epilogue* e, const void* x, void* y, cudaStream_t st);
+int read_status_fused_tc(int clear);
 int build_adjoint(const AxisP& A, AdjAxis* J);
 
 // non-separable 2D kernels (fcfs_full2d.cu)

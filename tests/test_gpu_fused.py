@@ -1,5 +1,6 @@
-"""GPU parity of the fused FCFS + 1x1 mix + bias + activation kernel against the
-FP64 oracle's resize_fused (pinned on the CPU to the library construction plus
+"""GPU parity of the fused FCFS + 1x1 mix + bias + activation kernels (the
+tensor-core mix for up to 96 input channels, the CUDA-core mix above that, the
+store epilogue without a mix) against the FP64 oracle's resize_fused (pinned on the CPU to the library construction plus
 torch's float64 1x1 convolution and activations).
 
 Bar per output channel o: |err| <= tol * (2 max|x| sum_c |mix[o][c]| + |bias[o]|)
@@ -81,7 +82,7 @@ def test_fused_mix_small(F, orc, ratios, method, pad, act):
     check(F, orc, (2, 3, 37, 71), ratios, method, pad, 5, act, pad_value=0.5, seed=act + 7 * method)
 
 
-@pytest.mark.parametrize("c_in,c_out", [(16, 40), (8, 32), (5, 33), (64, 64)])
+@pytest.mark.parametrize("c_in,c_out", [(16, 40), (8, 32), (5, 33), (64, 64), (96, 130), (100, 20)])
 def test_fused_mix_many_channels(F, orc, c_in, c_out):
     check(F, orc, (2, c_in, 29, 50), ((2, 1), (2, 1)), BICUBIC, REFL, c_out, 1, seed=c_in)
 
