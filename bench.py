@@ -386,6 +386,31 @@ def extras(fcfs, inputs, device, stream, peak, tune=True):
                              "hbm_frac": (x3.numel() + y3.numel()) * 2 / tdx / 1e9 / peak}
     out["c3_bf16_bwd_dx_dw"] = {"ms": tb * 1e3, "Gpix_s": px3 / tb / 1e9,
                                 "hbm_frac": (2 * x3.numel() + y3.numel()) * 2 / tb / 1e9 / peak}
+    # the whole c3 step (forward, input gradient, both weight gradients) captured in one CUDA graph
+    d3 = fcfs.make_desc(s3, ax, fcfs.FCFS_BF16, fcfs.FCFS_BF16)
+    ws3_bytes = fcfs.fcfs_backward_workspace(d3)
+    ws3 = torch.empty(max(ws3_bytes, 1), dtype=torch.uint8, device=device)
+    gx3 = torch.empty_like(x3)
+    gw3 = [torch.empty_like(a.w) for a in ax]
+
+    def c3_step():
+        st3 = torch.cuda.current_stream(device).cuda_stream
+        fcfs.fcfs_forward(d3, x3.data_ptr(), y3.data_ptr(), st3)
+        fcfs.fcfs_backward(d3, x3.data_ptr(), g3.data_ptr(), gx3.data_ptr(), [w.data_ptr() for w in gw3],
+                           ws3.data_ptr(), ws3_bytes, st3)
+
+    side3 = torch.cuda.Stream(device)
+    side3.wait_stream(stream)
+    with torch.cuda.stream(side3):
+        c3_step()
+        graph3 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph3, stream=side3):
+            c3_step()
+    stream.wait_stream(side3)
+    tg = timed(graph3.replay, steps, stream) / steps
+    out["c3_bf16_graph_fwd_bwd_step"] = {"ms": tg * 1e3, "Gpix_s": px3 / tg / 1e9,
+                                         "hbm_frac": 3 * (x3.numel() + y3.numel()) * 2 / tg / 1e9 / peak}
+    del graph3, gx3, gw3, ws3
     del x3, y3, g3
     # c5: 1x3x8192^2 bicubic 7/5 and 256^3 trilinear 3/2, fp32 forward and input gradient
     for key, spec, axes_n in (("c5_8192_bicubic_7_5", inputs.C5_2D, 2), ("c5_256cube_trilinear_3_2", inputs.C5_3D, 3)):
