@@ -58,6 +58,8 @@ def parse():
                         "input gradient of that c2 op (fp32), with --batch images")
     p.add_argument("--volume", action="store_true",
                    help="time only the c5 volume (1x1x256^3 fp32, trilinear 3/2): forward and input gradient")
+    p.add_argument("--d6", action="store_true",
+                   help="context run: 1x3x1024^2, 12 factors x 3 methods, libfcfs vs torch interpolate")
     p.add_argument("--fused", action="store_true",
                    help="time only the fused resize + 1x1 conv + ReLU decoder block (8x64x256^2, x2), "
                         "fused and unfused, in --dtype")
@@ -558,6 +560,43 @@ def fused_only(args, device):
           flush=True)
 
 
+D6_UP = [(3, 2), (5, 4), (4, 3), (2, 1), (5, 2), (27, 11)]
+D6_DOWN = [(2, 3), (4, 5), (3, 4), (1, 2), (2, 5), (2, 11)]
+
+
+def d6_only(args, device):
+    """Context for the paper's runtime claim (Sec. 6: the layer about as fast as the framework's resize):
+    a synthetic 1x3x1024x1024 FP32 image (the CelebA size), six up and six down factors, three methods;
+    libfcfs against torch.nn.functional.interpolate with the same sample convention (half-pixel centres,
+    Keys a = -0.75 for bicubic, floor for nearest), both timed with CUDA events."""
+    from paper_2203_10670_gb300 import build as B
+
+    B.build()
+    import torch.nn.functional as TF
+    from paper_2203_10670_gb300 import fcfs, inputs
+
+    stream = torch.cuda.current_stream(device)
+    x = inputs.uniform((1, 3, 1024, 1024), 11, device=device)
+    rows = []
+    modes = ((fcfs.NEAREST, "nearest", fcfs.ALIGN_FLOOR), (fcfs.BILINEAR, "bilinear", fcfs.ALIGN_HALF_PIXEL),
+             (fcfs.BICUBIC, "bicubic", fcfs.ALIGN_HALF_PIXEL))
+    for r, s_ in D6_UP + D6_DOWN:
+        for m, name, align in modes:
+            ax = [fcfs.Axis(r, s_, m)] * 2
+            y = fcfs.resize(x, ax, align=align, cubic_a=-0.75)
+            kw = {} if name == "nearest" else {"align_corners": False}
+            ref = TF.interpolate(x, scale_factor=r / s_, mode=name, **kw)
+            if tuple(ref.shape) != tuple(y.shape):
+                continue
+            tf = timed(lambda: fcfs.resize(x, ax, out=y, align=align, cubic_a=-0.75), args.steps, stream) / args.steps
+            tt = timed(lambda: TF.interpolate(x, scale_factor=r / s_, mode=name, **kw), args.steps, stream) / args.steps
+            rows.append({"ratio": f"{r}/{s_}", "method": name, "fcfs_ms": tf * 1e3, "interpolate_ms": tt * 1e3,
+                         "max_abs_diff": float((y - ref).abs().max())})
+    ratio = float(np.exp(np.mean([np.log(q["fcfs_ms"] / q["interpolate_ms"]) for q in rows])))
+    print(json.dumps({"mode": "d6: 1x3x1024^2 fp32, 12 factors x 3 methods, fcfs vs torch interpolate",
+                      "geomean_time_ratio_fcfs_over_interpolate": ratio, "cases": rows}), flush=True)
+
+
 def full2d_only(args, device):
     from paper_2203_10670_gb300 import build as B
 
@@ -703,6 +742,9 @@ def main():
             return
         if args.fused:
             fused_only(args, device)
+            return
+        if args.d6:
+            d6_only(args, device)
             return
         run_ours(args, rank, world, device)
     finally:
