@@ -115,12 +115,35 @@ def out_len(n: int, r: int, s: int) -> int:
     return (n * r) // s
 
 
+_DESC_CACHE: "dict" = {}
+_DESC_CACHE_MAX = 256
+
+
 def make_desc(shape: Sequence[int], axes: Sequence[Axis], dtype_in: int, dtype_out: int,
               pad: int = PAD_REPLICATE, pad_value: float = 0.0, align: int = ALIGN_PAPER,
               cubic_a: float = 0.0) -> N.fcfs_desc:
     """Descriptor for an input of shape [n, c, *spatial] (spatial outermost first).
     align / cubic_a: sample alignment and Keys parameter of the fixed methods
-    (ALIGN_PAPER and 0 = the paper's -0.5 by default)."""
+    (ALIGN_PAPER and 0 = the paper's -0.5 by default).
+
+    Descriptors are cached by their arguments (a learnable axis by its weight
+    tensor's address and shape); each call returns its own copy."""
+    key = (tuple(int(v) for v in shape),
+           tuple((a.r, a.s, a.method, a.K, None if a.w is None else (a.w.data_ptr(), tuple(a.w.shape), a.w.dtype,
+                                                                      a.w.is_cuda, a.w.is_contiguous()))
+                 for a in axes),
+           dtype_in, dtype_out, pad, float(pad_value), int(align), float(cubic_a))
+    hit = _DESC_CACHE.get(key)
+    if hit is not None:
+        return N.fcfs_desc.from_buffer_copy(hit)
+    d = _build_desc(shape, axes, dtype_in, dtype_out, pad, pad_value, align, cubic_a)
+    if len(_DESC_CACHE) >= _DESC_CACHE_MAX:
+        _DESC_CACHE.clear()
+    _DESC_CACHE[key] = N.fcfs_desc.from_buffer_copy(d)
+    return d
+
+
+def _build_desc(shape, axes, dtype_in, dtype_out, pad, pad_value, align, cubic_a) -> N.fcfs_desc:
     nd = len(shape) - 2
     if nd != len(axes) or not 1 <= nd <= 3:
         raise ValueError(f"{len(axes)} axes for a tensor with {nd} spatial dims")
