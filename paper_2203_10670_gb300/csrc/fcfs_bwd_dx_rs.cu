@@ -250,12 +250,8 @@ cudaError_t run_rs(const TmaDxParams& T, cudaStream_t st) {
         const size_t smem = (size_t)T.bar_off + 8 * T.stages;
         auto k = fcfs_bwd_dx2d_rs<S, SPAN, VW, Tg, Tg, true>;
         if (T.WAcap > T.threads) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
+        int sms = 0, per_sm = 0;
+        cudaError_t e = resident_ctas((const void*)k, T.threads, smem, &sms, &per_sm);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);

@@ -198,12 +198,8 @@ template <int NT, typename Tg, typename Tx>
 cudaError_t run(const TmaDxParams& T, cudaStream_t st) {
     const size_t smem = (size_t)T.bar_off + 8 * T.stages;
     auto k = fcfs_bwd_dx2d_tma<NT, Tg, Tx>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
+    int sms = 0, per_sm = 0;
+    cudaError_t e = resident_ctas((const void*)k, T.threads, smem, &sms, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);

@@ -42,13 +42,6 @@ struct FusedParams {
     void* y;
 };
 
-__device__ __forceinline__ float activate(float v, int act, float alpha, float lo, float hi) {
-    if (act == FCFS_ACT_RELU) return fmaxf(v, 0.f);
-    if (act == FCFS_ACT_LEAKY_RELU) return v >= 0.f ? v : alpha * v;
-    if (act == FCFS_ACT_CLAMP) return fminf(fmaxf(v, lo), hi);
-    return v;
-}
-
 template <int NT, int OB, typename Tin>
 __global__ void __launch_bounds__(kFusedThreads) fcfs_fused2d(const __grid_constant__ FusedParams F) {
     extern __shared__ float smem[];
@@ -181,7 +174,7 @@ __global__ void __launch_bounds__(kFusedThreads) fcfs_fused2d(const __grid_const
             if (o >= nob) break;
             float v = acc[k][o];
             if (F.bias) v += __ldg(F.bias + o0 + o);
-            v = activate(v, F.act, F.alpha, F.lo, F.hi);
+            v = apply_act(v, F.act, F.alpha, F.lo, F.hi);
             const long long at = (n * F.c_out + o0 + o) * oplane + pos;
             if (F.dtype_out == FCFS_F32) store_f(static_cast<float*>(F.y) + at, v);
             else store_f(static_cast<__nv_bfloat16*>(F.y) + at, v);

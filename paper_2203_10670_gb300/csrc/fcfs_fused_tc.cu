@@ -53,13 +53,6 @@ struct TcParams {
     int b_off, w_off, in_off, h_off, bar_off;  // byte offsets in shared memory (A at 0)
 };
 
-__device__ __forceinline__ float act_apply(float v, int act, float alpha, float lo, float hi) {
-    if (act == FCFS_ACT_RELU) return fmaxf(v, 0.f);
-    if (act == FCFS_ACT_LEAKY_RELU) return v >= 0.f ? v : alpha * v;
-    if (act == FCFS_ACT_CLAMP) return fminf(fmaxf(v, lo), hi);
-    return v;
-}
-
 // float index of element (row, k) in a K-major operand with kch 4-channel chunks per row group
 __device__ __forceinline__ int op_index(int row, int k, int kch) {
     return (row >> 3) * (kch * 32) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
@@ -321,7 +314,7 @@ __global__ void __launch_bounds__(kTcThreads) fcfs_fused2d_tc(const __grid_const
                 if (px_ok && o < F.c_out) {
                     float val = tr[r * 16 + (hl ^ (r & 15))];
                     if (F.bias) val += __ldg(F.bias + o);
-                    val = act_apply(val, F.act, F.alpha, F.lo, F.hi);
+                    val = apply_act(val, F.act, F.alpha, F.lo, F.hi);
                     const long long at = (n * F.c_out + o) * oplane + (long long)oy * AX.n_out + oxg;
                     if (F.dtype_out == FCFS_F32) store_f(static_cast<float*>(F.y) + at, val);
                     else store_f(static_cast<__nv_bfloat16*>(F.y) + at, val);

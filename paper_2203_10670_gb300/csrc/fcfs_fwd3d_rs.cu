@@ -210,12 +210,8 @@ cudaError_t run_rs3(const TmaFwd3Params& T, cudaStream_t st) {
     const bool v2 = T.P.OX % 2 == 0 && no % 2 == 0 && y % (2 * sizeof(Tout)) == 0;
     if (!v2 || T.threads > 256) return cudaErrorInvalidValue;
     auto k = v4 ? fcfs_fwd3d_rs<R, SPAN, NT, Tin, Tout, 4> : fcfs_fwd3d_rs<R, SPAN, NT, Tin, Tout, 2>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
+    int sms = 0, per_sm = 0;
+    cudaError_t e = resident_ctas((const void*)k, T.threads, smem, &sms, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);

@@ -225,12 +225,8 @@ cudaError_t run_rs(const TmaFwdParams& T, cudaStream_t st) {
                       : xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, true, false> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 4, false, false>)
                 : (xv ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, true, true>
                       : xs ? fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, true, false> : fcfs_fwd2d_rs<R, SPAN, Tin, Tout, 2, false, false>);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T.threads, smem);
+    int sms = 0, per_sm = 0;
+    cudaError_t e = resident_ctas((const void*)k, T.threads, smem, &sms, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);

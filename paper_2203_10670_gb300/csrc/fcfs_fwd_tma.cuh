@@ -327,13 +327,9 @@ cudaError_t run(const TmaFwdParams& T, size_t smem, cudaStream_t st) {
     const bool v4 = T.P.OX % 4 == 0 && no % 4 == 0 && y % (4 * sizeof(Tout)) == 0;
     const bool v2 = T.P.OX % 2 == 0 && no % 2 == 0 && y % (2 * sizeof(Tout)) == 0;
     auto k = v4 ? fcfs_fwd2d_tma<NT, Tin, Tout, 4> : v2 ? fcfs_fwd2d_tma<NT, Tin, Tout, 2> : fcfs_fwd2d_tma<NT, Tin, Tout, 1>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int threads = T.threads;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    int sms = 0, per_sm = 0;
+    cudaError_t e = resident_ctas((const void*)k, threads, smem, &sms, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);

@@ -6,6 +6,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include <type_traits>
 
 #include <cuda.h>
@@ -46,12 +50,17 @@ struct Epi {
 
 __device__ __forceinline__ bool epi_on(const Epi& e) { return e.act != 0 || e.bias != nullptr; }
 
+// fcfs_act applied to v: relu max(v, 0), leaky relu v >= 0 ? v : alpha v, clamp min(max(v, lo), hi)
+__device__ __forceinline__ float apply_act(float v, int act, float alpha, float lo, float hi) {
+    if (act == FCFS_ACT_RELU) return fmaxf(v, 0.f);
+    if (act == FCFS_ACT_LEAKY_RELU) return v >= 0.f ? v : alpha * v;
+    if (act == FCFS_ACT_CLAMP) return fminf(fmaxf(v, lo), hi);
+    return v;
+}
+
 __device__ __forceinline__ float epi_apply(const Epi& e, int c, float v) {
     if (e.bias) v += e.bias[c];
-    if (e.act == FCFS_ACT_RELU) return fmaxf(v, 0.f);
-    if (e.act == FCFS_ACT_LEAKY_RELU) return v >= 0.f ? v : e.alpha * v;
-    if (e.act == FCFS_ACT_CLAMP) return fminf(fmaxf(v, e.lo), e.hi);
-    return v;
+    return apply_act(v, e.act, e.alpha, e.lo, e.hi);
 }
 
 // Forward launch parameters.  Axis 0 = D, 1 = H (y), 2 = W (x); missing axes
@@ -232,6 +241,44 @@ struct NearestParams {
     const void* x;
     void* y;
 };
+
+// SMs of the current device and resident CTAs per SM for kernel `func` at
+// `threads` threads and `smem` dynamic shared-memory bytes.  Queried once per
+// (device, kernel, threads, bytes) and cached, so a launch costs no driver
+// queries after the first; the kernel's dynamic shared-memory limit is only
+// ever raised (to the largest size asked for so far).
+inline cudaError_t resident_ctas(const void* func, int threads, size_t smem, int* sms, int* per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    using Key = std::tuple<int, const void*, int, size_t>;
+    static std::mutex mu;
+    static std::map<Key, std::pair<int, int>> cache;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    const Key key{dev, func, threads, smem};
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *sms = it->second.first;
+        *per_sm = it->second.second;
+        return cudaSuccess;
+    }
+    size_t& lim = limit[{dev, func}];
+    if (smem > lim) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        lim = smem;
+    }
+    int n = 0, p = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, func, threads, smem);
+    if (e != cudaSuccess) return e;
+    cache[key] = {n, p};
+    *sms = n;
+    *per_sm = p;
+    return cudaSuccess;
+}
 
 __host__ __device__ inline int ext_index(int q, int n, int pad) {
     if ((unsigned)q < (unsigned)n) return q;
