@@ -221,3 +221,17 @@ def test_fused_epilogue_errors(native):
     assert run() == native.FCFS_ERR_UNSUPPORTED  # r_y r_x > 512
     d = fcfs.make_desc((1, 1, 8, 8, 8), [fcfs.Axis(2, 1, 1)] * 3, 0, 0)
     assert run() == native.FCFS_ERR_UNSUPPORTED  # 3D
+
+
+def test_descriptor_cache_returns_copies(native):
+    """make_desc caches descriptors by their arguments; each call gets its own copy, so changing one
+    (as several tests here do) never leaks into the next call."""
+    from paper_2203_10670_gb300 import fcfs
+
+    ax = [fcfs.Axis(3, 2, 1), fcfs.Axis(4, 3, 2)]
+    a = fcfs.make_desc((2, 3, 50, 60), ax, native.FCFS_F32, native.FCFS_BF16)
+    a.pad, a.axis[0].r = 2, 7
+    b = fcfs.make_desc((2, 3, 50, 60), ax, native.FCFS_F32, native.FCFS_BF16)
+    assert (b.pad, b.axis[0].r, b.axis[1].s, b.out_shape[0], b.out_shape[1]) == (0, 3, 3, 75, 80)
+    c = fcfs.make_desc((2, 3, 50, 60), ax, native.FCFS_F32, native.FCFS_BF16, pad=1, pad_value=0.5)
+    assert (c.pad, c.pad_value) == (1, 0.5) and b.pad == 0
