@@ -235,3 +235,19 @@ def test_descriptor_cache_returns_copies(native):
     assert (b.pad, b.axis[0].r, b.axis[1].s, b.out_shape[0], b.out_shape[1]) == (0, 3, 3, 75, 80)
     c = fcfs.make_desc((2, 3, 50, 60), ax, native.FCFS_F32, native.FCFS_BF16, pad=1, pad_value=0.5)
     assert (c.pad, c.pad_value) == (1, 0.5) and b.pad == 0
+
+
+def test_binding_argument_checks_for_the_new_layers():
+    """resize_full2d / resize_fused validate their tensors before any device work."""
+    import torch
+
+    from paper_2203_10670_gb300 import fcfs
+
+    x = torch.zeros(1, 3, 8, 8)
+    ax = [fcfs.Axis(2, 1, 1), fcfs.Axis(2, 1, 1)]
+    with pytest.raises(ValueError):  # weights must live on the device
+        fcfs.make_desc_full2d(x.shape, ax, torch.zeros(3, 2, 2, 3, 3), 0, 0)
+    with pytest.raises(ValueError):  # a non-separable layer has two spatial axes
+        fcfs.make_desc_full2d((1, 3, 8, 8, 8), ax + [fcfs.Axis(2, 1, 1)], torch.zeros(2, 2, 3, 3), 0, 0)
+    with pytest.raises(ValueError):  # the mix must live on the device
+        fcfs.resize_fused(x, ax, mix=torch.zeros(4, 3))
