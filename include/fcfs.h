@@ -2,18 +2,18 @@
  * libfcfs -- Fully Convolutional Fractional Scaling (FCFS) on GB300 (sm_103a).
  *
  * FCFS (Soloveitchik & Werman, arXiv 2203.10670) scales a signal by a rational
- * factor r/s in one layer: pad the input (Sec. 3.1), apply a convolution with
+ * factor r/s in one layer: pad the input (Sec. 3), apply a convolution with
  * r output channels and stride s whose kernels are interpolation weights
- * (Sec. 3.2), then pixel-shuffle the r channels into one output axis.  In 2D
+ * (Sec. 3.1), then pixel-shuffle the r channels into one output axis.  In 2D
  * and 3D (Sec. 4) the convolution has prod(r_a) channels and a per-axis
  * stride, followed by an N-d pixelshuffle.  This library evaluates that layer
- * as one fused polyphase gather: the r-channel hidden layer of Sec. 3.2 is
+ * as one fused polyphase gather: the r-channel hidden layer of Sec. 3.1 is
  * never written to memory, the pixelshuffle is the store index.
  *
  * Conventions used by every entry point:
  *   - Geometry per spatial axis with input length N: output length
  *     No = floor(N r / s); output o = i r + j (window i, phase j) samples the
- *     input at p = o s / r (Sec. 3.2: phase j of window i interpolates at
+ *     input at p = o s / r (Sec. 3.1: phase j of window i interpolates at
  *     offset i + j/r in stride units).  A window of T = 2K+1 taps starts at
  *     input index i s - L with L = K - floor(s/2).
  *   - Tensors are contiguous row-major [n][c][spatial...], the last spatial
@@ -51,14 +51,14 @@ typedef enum {
  * a = -0.5 (the printed kernel's "-4a" constant is +2). */
 typedef enum { FCFS_NEAREST = 0, FCFS_BILINEAR = 1, FCFS_BICUBIC = 2 } fcfs_method;
 
-/* Padding of Sec. 3.1: repetition of edge pixels, a constant c (zeros when
+/* Padding of Sec. 3: repetition of edge pixels, a constant c (zeros when
  * c = 0), and reflection about the edge sample (edge not repeated; any
  * distance by periodic mirroring with period 2(N-1)). */
 typedef enum { FCFS_PAD_REPLICATE = 0, FCFS_PAD_CONSTANT = 1, FCFS_PAD_REFLECT = 2 } fcfs_pad;
 
 /* Sample alignment of the fixed methods (learnable weights define their own
  * taps and ignore it):
- *   FCFS_ALIGN_PAPER       output o samples p = o s / r (Sec. 3.2: phase j of
+ *   FCFS_ALIGN_PAPER       output o samples p = o s / r (Sec. 3.1: phase j of
  *                          window i at offset i + j/r in stride units); nearest
  *                          takes floor(p + 1/2) (Sec. 5.2.1 examples)
  *   FCFS_ALIGN_HALF_PIXEL  pixel centres: p = (o + 1/2) s / r - 1/2; nearest
@@ -77,7 +77,7 @@ typedef enum { FCFS_F32 = 0, FCFS_BF16 = 1, FCFS_U8 = 2 } fcfs_dtype;
 #define FCFS_MAX_TAPS 9    /* largest T = 2K+1 for learnable weights */
 
 /*
- * Weight table of Sec. 5.2 (Sec. 3.2 "kernel_weights").  Writes the r x (2K+1)
+ * Weight table of Sec. 5.2 (Sec. 3.1 "kernel_weights").  Writes the r x (2K+1)
  * FP32 table W[j][m] = k(j s / r - (m - L)) to HOST memory w_out (row j =
  * phase), where k is the bilinear hat or the Keys kernel; nearest is one-hot
  * at m = floor((2 j s + r) / (2 r)) + L (round half up, the rounding the
@@ -90,7 +90,7 @@ typedef enum { FCFS_F32 = 0, FCFS_BF16 = 1, FCFS_U8 = 2 } fcfs_dtype;
 int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out);
 
 /*
- * Geometry of one axis (Sec. 3.2 "Description"): for input length n_in,
+ * Geometry of one axis (Sec. 3.1.1 "Description"): for input length n_in,
  * *n_out = floor(n_in r / s), *n_windows = ceil(n_out / r), *left_offset = L.
  * K = 0 selects K_min for `method`.  Any output pointer may be NULL.
  */
@@ -130,7 +130,7 @@ typedef struct {
 /*
  * Non-separable 2D kernels (w2d != NULL): the 2D convolution of Sec. 4 with a
  * general T_y x T_x kernel per phase pair instead of the outer product of the
- * two axis kernels, so that learning can change the kernel's shape (Sec. 6):
+ * two axis kernels, so that learning can change the kernel's shape (Sec. 7):
  *   y[n,c, iy r_y + jy, ix r_x + jx] = sum_{my,mx} w2d[c][jy][jx][my][mx]
  *                                      x~[n,c, iy s_y - L_y + my, ix s_x - L_x + mx]
  * Requires ndim == 2 and axis[a].w == NULL; axis[a] gives r, s and K (0 = K_min
@@ -142,7 +142,7 @@ typedef struct {
  */
 
 /*
- * Forward FCFS (Sec. 3.2 pseudocode; Sec. 4 for 2D/3D):
+ * Forward FCFS (Sec. 3.1 pseudocode; Sec. 4 for 2D/3D):
  *   y[n,c,o] = sum_m prod_a W_a[c][j_a][m_a] x~[n,c, i_a s_a - L_a + m_a]
  * with o_a = i_a r_a + j_a.  x: DEVICE [n][c][in_shape...] of dtype_in;
  * y: DEVICE [n][c][out_shape...] of dtype_out, fully overwritten.  x and y
@@ -186,7 +186,7 @@ int fcfs_forward_fused(const fcfs_desc* d, const fcfs_epilogue* e, const void* x
 size_t fcfs_backward_workspace(const fcfs_desc* d);
 
 /*
- * Backward of the forward map above (the learnable-weights remark of Sec. 6
+ * Backward of the forward map above (the learnable-weights remark of Sec. 7
  * needs both gradients):
  *   gx = adjoint of the polyphase map applied to gy, with the pad adjoint
  *        folded in (replicate sends every virtual index to the edge pixel,
@@ -205,6 +205,26 @@ size_t fcfs_backward_workspace(const fcfs_desc* d);
  */
 int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw,
                   void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * Tile-shape search for the planned forward (the plan/autotune step; the paper
+ * has no counterpart: it chooses how the Sec. 3.1 / Sec. 4 layer is tiled on
+ * the GPU, not what it computes).  Times the default tile and a candidate set
+ * (output columns x rows per tile, CTA size, register-blocked or not; depth
+ * windows for 3D) on the caller's x and y, reps launches each, synchronously,
+ * and stores the fastest in a process-wide plan cache keyed by (ndim, r, s
+ * per axis, taps, tap offsets, dtypes) that later fcfs_forward calls with the
+ * same key use.  Every candidate computes the same result; y is overwritten.
+ * reps < 1 selects 3.  *best_ms (may be NULL) receives the best time per call,
+ * *n_candidates (may be NULL) the number timed.  Must not be called while
+ * `stream` is being captured (FCFS_ERR_ARG).  Errors: as fcfs_forward;
+ * FCFS_ERR_UNSUPPORTED for non-separable (w2d) descriptors.
+ */
+int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, void* stream, int reps, float* best_ms,
+                      int* n_candidates);
+
+/* Forget every plan fcfs_tune_forward stored (later calls use the default tiles). */
+void fcfs_clear_plans(void);
 
 /*
  * Status word written by the device code: 0 when every bounded wait of the
@@ -285,8 +305,8 @@ int fcfs_serve_create(const fcfs_serve_config* cfg, void* stream, void** handle)
 
 /* Queue one request: d describes a 2D resize with fixed methods; x is DEVICE
  * input (F32, BF16 or U8), kept valid until the request completes; y is DEVICE
- * output or NULL to place it in the pool (then d->dtype_out must equal the
- * server's out_dtype).  arrival_s (fcfs_serve_clock time) is the time latency
+ * output or NULL to place it in the pool.  d->dtype_out must equal the
+ * server's out_dtype in both cases (FCFS_ERR_ARG otherwise).  arrival_s (fcfs_serve_clock time) is the time latency
  * is measured from.  *req_id receives the id.  FCFS_ERR_NOMEM when the output
  * could never fit the pool; FCFS_ERR_ARG / FCFS_ERR_UNSUPPORTED for bad
  * descriptors. */

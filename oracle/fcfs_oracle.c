@@ -16,8 +16,8 @@
  * (r = s = 1, one tap of weight 1), which leaves every sum unchanged.
  *
  * What is computed (per spatial axis, readings of the paper in brackets):
- *   - output length No = floor(N r / s)                     [Sec. 3.2 "Description"; floor reading]
- *   - output o samples the input at p = o s / r             [Sec. 3.2: phase j of window i at i + j/r, stride units]
+ *   - output length No = floor(N r / s)                     [Sec. 3.1.1 "Description"; floor reading]
+ *   - output o samples the input at p = o s / r             [Sec. 3.1: phase j of window i at i + j/r, stride units]
  *   - direct formula: y(p) = sum_t k(p - t) x~[t]           [Sec. 5.2, bilinear and Keys kernels]
  *     nearest: x~[floor(p + 1/2)] in exact integers         [Sec. 5.2.1 examples: rounding, ties upward]
  *   - sample-alignment variants (not the paper's; the conventions of common
@@ -26,12 +26,12 @@
  *       floor nearest x~[floor(o s / r)] (linear/cubic as the paper's p)
  *     and the Keys parameter a (the paper's kernel has a = -1/2).
  *   - polyphase form with explicit weights W[j][m]:
- *     y[i r + j] = sum_m W[j][m] x~[i s - L + m]            [Sec. 3.2 pseudocode: pad, conv(stride s, r outputs), pixelshuffle]
+ *     y[i r + j] = sum_m W[j][m] x~[i s - L + m]            [Sec. 3.1 pseudocode: pad, conv(stride s, r outputs), pixelshuffle]
  *     window half width K >= K_min, T = 2K + 1, L = K - floor(s/2)
- *   - x~ is the padded (extended) signal: replicate, constant, reflect [Sec. 3.1 "Padding"]
+ *   - x~ is the padded (extended) signal: replicate, constant, reflect [Sec. 3 "Stride, Padding & Pixelshuffle"]
  *   - ND: tensor product of the per-axis weights, ND extension  [Sec. 4, ND FCFS]
  *   - adjoint (input gradient) and weight gradient of the polyphase form
- *     (the paper's Sec. 6 "learn the weights" remark needs both).
+ *     (the paper's Sec. 7 "learn the weights" remark needs both).
  *
  * Parity notes: the printed bicubic 3x3 matrices of Sec. 5.2.3 are not
  * reproduced by any Keys weight vector; they are not used (parity unpinned

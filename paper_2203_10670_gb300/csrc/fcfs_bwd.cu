@@ -1,5 +1,5 @@
-// Backward FCFS kernels (gradients of the Sec. 3.2 / Sec. 4 layer, needed
-// to learn the kernel weights as Sec. 6 proposes):
+// Backward FCFS kernels (gradients of the Sec. 3.1 / Sec. 4 layer, needed
+// to learn the kernel weights as Sec. 7 proposes):
 //   K4 fcfs_bwd_dx2d / fcfs_bwd_dx3d - input gradient as a gather: the
 //        pixel-unshuffle and the transposed strided convolution are one
 //        polyphase pass per axis, followed by the pad adjoint (fold);

@@ -119,6 +119,7 @@ __device__ __forceinline__ int depth_target(const TmaDx3Params& T, int v) {
 template <int NT, typename Tg, typename Tx>
 __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constant__ TmaDx3Params T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     __shared__ CursorDx3 cur;
     const AdjP &JD = T.aj[0], &JY = T.aj[1], &JX = T.aj[2];
     float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constan
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
+        s_abort = 0;
         cur.tile = t_begin;
         cur.g = dx3_geo(T, t_begin);
         while (cur.g.g_last < cur.g.g_first && ++cur.tile < t_end) cur.g = dx3_geo(T, cur.tile);
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constan
     int cur_c = -1;
     int stg = 0;         // stage of the current job
     uint32_t phase = 0;  // its barrier phase
+    int consumed = 0;    // jobs taken so far (cur.n were issued)
     for (int tile = t_begin; tile < t_end; ++tile) {
         const Dx3Geo gt = dx3_geo(T, tile);
         Tx* xpl = static_cast<Tx*>(T.gx) + (long long)gt.plane * Nd * Ny * Nx;
@@ -199,8 +202,13 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constan
         for (int gd = gt.g_first; gd <= gt.g_last; ++gd) {
             unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
             // one warp waits for the copy; the barrier releases the others
-            if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
+            if (threadIdx.x < 32 && !mbar_wait(&bars[stg], phase, &g_status_bwd_tma)) s_abort = 1;
             __syncthreads();
+            if (s_abort) {
+                if (threadIdx.x == 0) drain_ring(bars, S, stg, phase, cur.n - consumed, &g_status_bwd_tma);
+                return;
+            }
+            ++consumed;
             const Tg* G0 = reinterpret_cast<const Tg*>(bufk);
             float* slot = ring + rslot * plane_sz;
             if (gd < 0 || gd >= JD.n_g) {

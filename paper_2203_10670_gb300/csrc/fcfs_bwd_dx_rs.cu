@@ -43,6 +43,7 @@ template <int S, int SPAN, int VW, typename Tg, typename Tx, bool XSPEC>
 __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
     constexpr int SPANX = (SPAN + VW - 1) / VW * VW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     __shared__ float sWFx[S * SPANX], sWFy[S * SPAN];
     const AdjP& JX = T.aj[2];
     const AdjP& JY = T.aj[1];
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
     if (threadIdx.x == 0) {
         for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
+        s_abort = 0;
         dx_walk_init(T, walk, tile);
         for (int k = 0; k < NS && tile + k < tile_end; ++k) {
             sgeo[k] = dx_walk_geo(T, walk);
@@ -86,8 +88,12 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
         unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
         const Tg* G0 = reinterpret_cast<const Tg*>(bufk);
         // one warp waits for the copy; the barrier releases the others
-        if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
+        if (threadIdx.x < 32 && !mbar_wait(&bars[stg], phase, &g_status_bwd_tma)) s_abort = 1;
         __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0) drain_ring(bars, NS, stg, phase, min(NS, tile_end - tile), &g_status_bwd_tma);
+            return;
+        }
         const DxGeo geo = sgeo[stg];
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
             // the previous tile ended with a barrier: no thread still reads the weights

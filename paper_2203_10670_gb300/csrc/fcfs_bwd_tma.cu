@@ -1,6 +1,6 @@
 // K4 (fast path): persistent, TMA-staged input gradient of the FCFS layer
-// for 1D/2D (the adjoint of the Sec. 3.2 / Sec. 4 map, needed to learn the
-// weights as Sec. 6 proposes).
+// for 1D/2D (the adjoint of the Sec. 3.1 / Sec. 4 map, needed to learn the
+// weights as Sec. 7 proposes).
 //
 // The adjoint of one axis is itself a polyphase operator: its window a has s
 // phases u whose outputs are the extended input indices v = a*s + lo_out + u,
@@ -36,6 +36,7 @@ __device__ __forceinline__ void stage_adj_weights(float* dst, const AxisP& A, co
 template <int NT, typename Tg, typename Tx>
 __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__ TmaDxParams T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     const AdjP& JX = T.aj[2];
     const AdjP& JY = T.aj[1];
     float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
+        s_abort = 0;
         dx_walk_init(T, walk, tile);
         for (int k = 0; k < S && tile + k < tile_end; ++k) {
             sgeo[k] = dx_walk_geo(T, walk);
@@ -78,8 +80,12 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
     for (; tile < tile_end; ++tile) {
         unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
         // one warp waits for the copy; the barrier releases the others
-        if (threadIdx.x < 32) mbar_wait(&bars[stg], phase, &g_status_bwd_tma);
+        if (threadIdx.x < 32 && !mbar_wait(&bars[stg], phase, &g_status_bwd_tma)) s_abort = 1;
         __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0) drain_ring(bars, S, stg, phase, min(S, tile_end - tile), &g_status_bwd_tma);
+            return;
+        }
         const DxGeo geo = sgeo[stg];
         const int VX = geo.X.vhi - geo.X.vlo + 1;
         const int VY = geo.Y.vhi - geo.Y.vlo + 1;
@@ -349,6 +355,7 @@ __device__ __forceinline__ void dw_fix_edges(const TmaDwParams& T, const DwGeo& 
 template <int NT, typename Tv>
 __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__ TmaDwParams T, const void* xptr) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     const FwdParams& P = T.P;
     const AxisP& AY = P.ax[1];
     const AxisP& AX = P.ax[2];
@@ -386,6 +393,7 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_barrier_init();
+        s_abort = 0;
     }
     __syncthreads();
     const int per = (T.ntiles + gridDim.x - 1) / gridDim.x;
@@ -453,8 +461,12 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
         Tv* X = xb(k & 1);
         const Tv* Gt = gb(k & 1);
         // one warp waits for the copies; the barrier releases the others
-        if (threadIdx.x < 32) mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        if (threadIdx.x < 32 && !mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma)) s_abort = 1;
         __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0) drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), 1, &g_status_bwd_tma);
+            return;
+        }
         const DwGeo geo = sgeo[k & 1];
         if (threadIdx.x == 0 && tile + 1 < tile_end) issue(tile + 1, (k + 1) & 1);  // the other slot
         const int ch = per_channel ? geo.c : 0;
@@ -564,6 +576,7 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dw2d_tma(const __grid_constant__
 template <int R, int NT, typename Tv>
 __global__ void __launch_bounds__(256, 2) fcfs_bwd_dw2d_rb(const __grid_constant__ TmaDwParams T, const void* xptr) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     __shared__ float sWx[R * NT], sWy[R * NT];
     __shared__ DwGeo sgeo[2];
     const FwdParams& P = T.P;
@@ -598,6 +611,7 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dw2d_rb(const __grid_constant
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_barrier_init();
+        s_abort = 0;
     }
     __syncthreads();
     const int per = (T.ntiles + gridDim.x - 1) / gridDim.x;
@@ -643,8 +657,12 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dw2d_rb(const __grid_constant
         Tv* X = xb(k & 1);
         const Tv* Gt = gb(k & 1);
         // one warp waits for the copies; the barrier releases the others
-        if (threadIdx.x < 32) mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma);
+        if (threadIdx.x < 32 && !mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_bwd_tma)) s_abort = 1;
         __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0) drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), 1, &g_status_bwd_tma);
+            return;
+        }
         const DwGeo geo = sgeo[k & 1];
         if (threadIdx.x == 0 && tile + 1 < tile_end) issue(tile + 1, (k + 1) & 1);  // the other slot
         const int ch = per_channel ? geo.c : 0;

@@ -1,7 +1,7 @@
 // Non-separable 2D FCFS: the 2D convolution of Sec. 4 with one general
 // T_y x T_x kernel per phase pair (j_y, j_x) instead of the outer product of
 // two axis kernels, the learnable form that lets training change the shape of
-// the interpolation kernel (Sec. 6):
+// the interpolation kernel (Sec. 7):
 //   y[n,c, iy r_y + jy, ix r_x + jx] = sum_{my,mx} W[c][jy][jx][my][mx]
 //                                      x~[n,c, iy s_y - L_y + my, ix s_x - L_x + mx]
 //   K7 fcfs_full2d_fwd       - padded input tile staged through the index map

@@ -1,9 +1,9 @@
-// Forward FCFS kernels (Sec. 3.2 pseudocode, Sec. 4 for N-d):
+// Forward FCFS kernels (Sec. 3.1 pseudocode, Sec. 4 for N-d):
 //   K1 fcfs_fwd2d  - fused separable polyphase gather for 1D/2D
 //   K3 fcfs_fwd3d  - the same with a depth-streaming ring of planes
 //   K2 fcfs_nearest - nearest on every axis: an exact gather copy
 //
-// The r-channel hidden layer of Sec. 3.2 (shape r x N/s per axis) is never
+// The r-channel hidden layer of Sec. 3.1 (shape r x N/s per axis) is never
 // stored: a CTA stages an input tile (with the padding rule applied as an
 // index map), runs the x taps into a shared-memory FP32 intermediate, runs the
 // y taps from there, and writes each output at its pixel-shuffled position.

@@ -13,6 +13,7 @@ namespace {
 template <int NT, typename Tin, typename Tout>
 __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_tma(const __grid_constant__ TmaFwd3Params T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     __shared__ Cursor3 cur;
     const FwdParams& P = T.P;
     const AxisP &AD = P.ax[0], &AY = P.ax[1], &AX = P.ax[2];
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_tma(const __grid_constant__
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
+        s_abort = 0;
         cur.tile = t_begin;
         cur.g = geo3(T, t_begin);
         cur.p = cur.g.p_first;
@@ -48,6 +50,7 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_tma(const __grid_constant__
     int cur_c = -1;
     int k = 0;           // stage of the current job
     uint32_t phase = 0;  // its barrier phase
+    int consumed = 0;    // jobs taken so far (cur.n were issued)
     for (int tile = t_begin; tile < t_end; ++tile) {
         const Geo3 geo = geo3(T, tile);
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
@@ -62,8 +65,13 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_tma(const __grid_constant__
         for (int p = geo.p_first; p <= geo.p_last; ++p) {
             Tin* buf = reinterpret_cast<Tin*>(smem_raw + k * T.buf_bytes);
             // one warp waits for the copy; the barrier releases the others
-            if (threadIdx.x < 32) mbar_wait(&bars[k], phase, &g_status_fwd3d);
+            if (threadIdx.x < 32 && !mbar_wait(&bars[k], phase, &g_status_fwd3d)) s_abort = 1;
             __syncthreads();
+            if (s_abort) {
+                if (threadIdx.x == 0) drain_ring(bars, S, k, phase, cur.n - consumed, &g_status_fwd3d);
+                return;
+            }
+            ++consumed;
             const int sd = ext_index(p, AD.n_in, P.pad);
             if (sd < 0) {  // a whole plane of the constant
                 const Tin cv = from_f<Tin>(P.padv);

@@ -53,6 +53,7 @@ template <int R, int SPAN, typename Tin, typename Tout, int VW, bool XSPEC, bool
 __global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ TmaFwdParams T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ TileGeo sgeo[2];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     __shared__ float sWFx[R * SPAN], sWFy[R * SPAN];
     const FwdParams& P = T.P;
     const AxisP& AY = P.ax[1];
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ Tma
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_barrier_init();
+        s_abort = 0;
     }
     __syncthreads();
     const int ntiles = (int)T.ntiles;
@@ -98,8 +100,13 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ Tma
             sgeo[(k + 1) & 1] = tile_geo(T, tile + 1);
             issue_tile<Tin>(T, sgeo[(k + 1) & 1], (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
         }
-        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma);
+        if (!mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma)) s_abort = 1;
         __syncthreads();
+        if (s_abort) {  // uniform: read after the barrier; this tile's and the prefetched copy in flight
+            if (threadIdx.x == 0)
+                drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), tile + 1 < tile_end ? 2 : 1, &g_status_fwd_tma);
+            return;
+        }
         const TileGeo geo = sgeo[k & 1];
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
             stage_span_weights<R, SPAN>(sWFx, AX, geo.c);

@@ -1,7 +1,7 @@
 // Gather-staged forward tile shared by the 2D forward kernel and the
 // serving kernel: stage the padded input tile through the index map, run the
 // x taps into a shared-memory FP32 intermediate, run the y taps and store at
-// the pixel-shuffled output positions (Sec. 3.2; Sec. 4 per axis).
+// the pixel-shuffled output positions (Sec. 3.1; Sec. 4 per axis).
 #pragma once
 
 #include "fcfs_internal.cuh"

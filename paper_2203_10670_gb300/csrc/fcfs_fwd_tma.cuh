@@ -1,5 +1,5 @@
 // K1 (fast path, kernel templates): persistent, TMA-staged, double-buffered fused FCFS forward
-// for 1D/2D (Sec. 3.2 pseudocode; Sec. 4 with separable kernels).
+// for 1D/2D (Sec. 3.1 pseudocode; Sec. 4 with separable kernels).
 //
 // Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...  While it
 // computes tile k from one shared-memory buffer, the bulk-tensor copy of
@@ -188,6 +188,7 @@ template <int NT, typename Tin, typename Tout, int VW>
 __global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ TmaFwdParams T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ TileGeo sgeo[2];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
     const FwdParams& P = T.P;
     const AxisP& AY = P.ax[1];
     const AxisP& AX = P.ax[2];
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ Tm
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_barrier_init();
+        s_abort = 0;
     }
     __syncthreads();
 
@@ -242,8 +244,13 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ Tm
             sgeo[(k + 1) & 1] = tile_geo(T, tile + 1);
             issue_tile<Tin>(T, sgeo[(k + 1) & 1], (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
         }
-        mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma);
-        __syncthreads();  // TMA data and this tile's geometry visible to all
+        if (!mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {  // uniform: read after the barrier; this tile's and the prefetched copy in flight
+            if (threadIdx.x == 0)
+                drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), tile + 1 < tile_end ? 2 : 1, &g_status_fwd_tma);
+            return;
+        }  // TMA data and this tile's geometry visible to all
         const TileGeo geo = sgeo[k & 1];
         if (cur_c < 0 || (learn && geo.c != cur_c)) {  // per-channel (or fixed) taps
             for (int e = threadIdx.x; e < AX.r * NT; e += blockDim.x) {

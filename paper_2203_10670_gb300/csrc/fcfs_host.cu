@@ -1,5 +1,5 @@
 // libfcfs host side: the C ABI entry points, argument validation, the weight
-// and geometry tables of Sec. 3.2 / Sec. 5.2, and the tile planner.
+// and geometry tables of Sec. 3.1 / Sec. 5.2, and the tile planner.
 #include <math.h>
 
 #include <cmath>

@@ -272,8 +272,11 @@ int fcfs_serve_submit(void* h, const fcfs_desc* d, const void* x, void* y, doubl
     for (int a = 0; a < 2; ++a)
         if (d->axis[a].w) return fail(FCFS_ERR_UNSUPPORTED, "serving uses the fixed method tables");
     if (!x) return fail(FCFS_ERR_ARG, "x is NULL");
-    if (!y && d->dtype_out != sv->cfg.out_dtype)
-        return fail(FCFS_ERR_ARG, "pooled outputs use the server's out_dtype");
+    // every slot of a step is stored by the grouped kernel instantiated for the
+    // server's out_dtype, caller-placed outputs included
+    if (d->dtype_out != sv->cfg.out_dtype)
+        return fail(FCFS_ERR_ARG, "dtype_out %d differs from the server's out_dtype %d", d->dtype_out,
+                    sv->cfg.out_dtype);
     if (((uintptr_t)x) % dtype_size(d->dtype_in) || (y && ((uintptr_t)y) % dtype_size(d->dtype_out)))
         return fail(FCFS_ERR_ARG, "x or y not aligned to its element size");
     ServeSlot sl;

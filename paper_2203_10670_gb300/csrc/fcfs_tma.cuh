@@ -1,7 +1,8 @@
 // Bulk-tensor (TMA) copies and mbarrier waits for sm_100-class GPUs, in
 // inline PTX.  Every wait is bounded: when the iteration limit runs out the
-// kernel records FCFS_DEVERR_TIMEOUT in a device status word and carries on,
-// so no CTA can hang the GPU.
+// kernel records FCFS_DEVERR_TIMEOUT in a device status word, waits (bounded)
+// for the copies it still has in flight and returns, so no CTA can hang the
+// GPU and the first timeout ends the launch.
 #pragma once
 
 #include <cuda.h>
@@ -74,6 +75,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* s
         if (mbar_try_wait(bar, parity)) return true;
     atomicOr(status, FCFS_DEVERR_TIMEOUT);
     return false;
+}
+
+// After a bounded wait ran out, a kernel stops walking its tiles: the CTA
+// leaves at the next block-wide barrier.  Before it does, one thread waits
+// (again bounded) for the n copies the CTA still has in flight, held by ring
+// stages stg, stg+1, ... (mod S) starting at barrier phase `phase`, so that
+// no copy lands in shared memory after the CTA has exited.
+__device__ __forceinline__ void drain_ring(uint64_t* bars, int S, int stg, uint32_t phase, int n, int* status) {
+    for (int i = 0; i < n && i < S; ++i) {
+        int st = stg + i;
+        uint32_t ph = phase;
+        if (st >= S) {
+            st -= S;
+            ph ^= 1u;
+        }
+        mbar_wait(&bars[st], ph, status);
+    }
 }
 
 }  // namespace fcfs

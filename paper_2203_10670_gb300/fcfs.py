@@ -271,7 +271,7 @@ class FCFSFunction(torch.autograd.Function):
 
 
 class FCFS(torch.nn.Module):
-    """FCFS layer (Sec. 3.2 / Sec. 4): depthwise, separable per spatial axis.
+    """FCFS layer (Sec. 3.1 / Sec. 4): depthwise, separable per spatial axis.
 
     ratios: one (r, s) per spatial axis.  learnable=True gives each axis
     per-channel taps [C, r, 2K+1] initialised to the method's table."""

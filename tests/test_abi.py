@@ -43,6 +43,18 @@ def test_every_declared_symbol_is_exported(native):
     assert declared <= set(native.SIGNATURES), declared - set(native.SIGNATURES)
 
 
+def test_every_exported_entry_point_is_declared(native):
+    # the reverse direction: no fcfs_* function leaves the library undeclared
+    import subprocess
+
+    out = subprocess.run(["nm", "-D", "--defined-only", native.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {m.group(1) for m in re.finditer(r"\sT\s(fcfs_\w+)$", out, flags=re.M)}
+    assert "fcfs_forward" in exported
+    undeclared = sorted(exported - _declared_functions())
+    assert not undeclared, undeclared
+
+
 def test_status_strings(native):
     lib = native.load()
     assert lib.fcfs_status_string(0) == b"ok"

@@ -253,3 +253,31 @@ def test_config3_bf16_layer_full(F, orc):
 def test_config5_backward_dx(F, orc):
     # 3D trilinear 3/2 input gradient at full size
     check_dx(F, orc, inputs.C5_3D["shape"], [F.Axis(3, 2, BILINEAR)] * 3, REPL, seed=77)
+
+
+def test_config5_large_bicubic_7_5_dx_sampled(F, orc):
+    """1x3x8192^2 bicubic 7/5 input gradient (the per-output gather kernel at this ratio) against the
+    oracle's gather-form adjoint on 100,000 sampled input pixels plus the edge rows and columns."""
+    shape = inputs.C5_2D["shape"]
+    axes = [F.Axis(7, 5, BICUBIC)] * 2
+    g_shape = tuple(shape[:2]) + tuple(n * 7 // 5 for n in shape[2:])
+    gy = inputs.normal(g_shape, 78, device="cuda")
+    gx, _ = F.resize_backward(None, gy, axes, in_shape=shape, in_dtype=torch.float32)
+    torch.cuda.synchronize()
+    assert F.fcfs_device_status(clear=True) == 0
+    rng = np.random.default_rng(79)
+    H, W = shape[2], shape[3]
+    idx = list(rng.integers(0, int(np.prod(shape)), 100_000))
+    for p in (0, shape[1] - 1):
+        base = p * H * W
+        idx += [base + c for c in range(0, W, 16)] + [base + (H - 1) * W + c for c in range(0, W, 16)]
+        idx += [base + r * W for r in range(0, H, 16)] + [base + r * W + W - 1 for r in range(0, H, 16)]
+    idx = np.array(idx, dtype=np.int64)
+    go = gy.double().cpu().numpy()
+    oax = _oaxes(axes)
+    want = orc.adjoint_dx_at(go, shape[2:], oax, idx)
+    got = gx.reshape(-1)[torch.from_numpy(idx).cuda()].double().cpu().numpy()
+    scale = float(np.abs(go).max())
+    for a in _abs_axes(oax, orc):
+        scale *= float(a["w"].sum(-1).max())
+    assert np.abs(got - want).max() <= 2e-6 * scale

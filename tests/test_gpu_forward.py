@@ -228,7 +228,7 @@ def test_host_tensors_round_trip(F, orc):
     assert np.abs(y.double().numpy() - want).max() <= 2e-6
 
 
-def test_tuned_plan_same_result(F):
+def test_tuned_plan_same_result(F, orc):
     x = inputs.uniform((2, 3, 200, 300), 91).cuda()
     axes = [F.Axis(4, 3, BICUBIC)] * 2
     before = F.resize(x, axes)
@@ -240,9 +240,13 @@ def test_tuned_plan_same_result(F):
     F.fcfs_clear_plans()
     # tile shape changes the work split, never the arithmetic order of one output
     assert torch.equal(before, after)
+    # and the tuned plan's output against the oracle
+    xh = x.double().cpu().numpy()
+    want = orc.resize(xh, [dict(r=4, s=3, method=BICUBIC)] * 2)
+    assert np.abs(after.double().cpu().numpy() - want).max() <= 2e-6 * float(np.abs(xh).max())
 
 
-def test_tuned_plan_same_result_3d(F):
+def test_tuned_plan_same_result_3d(F, orc):
     x = inputs.uniform((1, 2, 40, 48, 64), 92).cuda()
     axes = [F.Axis(3, 2, BILINEAR)] * 3
     before = F.resize(x, axes)
@@ -253,6 +257,9 @@ def test_tuned_plan_same_result_3d(F):
     after = F.resize(x, axes)
     F.fcfs_clear_plans()
     assert torch.equal(before, after)
+    xh = x.double().cpu().numpy()
+    want = orc.resize(xh, [dict(r=3, s=2, method=BILINEAR)] * 3)
+    assert np.abs(after.double().cpu().numpy() - want).max() <= 2e-6 * float(np.abs(xh).max())
 
 
 # ---------------------------------------------------------- full-size configs

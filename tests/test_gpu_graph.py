@@ -1,7 +1,13 @@
-"""CUDA-graph capture of the differentiable layer: the forward, input gradient
-and weight gradients of the c3 layer (BF16, 5/4 learnable per-channel taps)
-captured in one graph replay bit for bit what the eager calls produce (every
-kernel is deterministic, the weight gradient included)."""
+"""CUDA-graph captures.
+
+* The differentiable layer: the forward, input gradient and weight gradients
+  of the c3 layer (BF16, 5/4 learnable per-channel taps) captured in one graph
+  replay bit for bit what the eager calls produce (every kernel is
+  deterministic, the weight gradient included).
+* The timed benchmark step itself (c2: 16x3x1080x1920, bicubic 2/3, bicubic
+  4/3, nearest 3/2, tiles chosen by the autotuner, one graph), built by the
+  same function bench.py times, replayed and checked against the FP64 oracle
+  on sampled outputs plus the edge rows and columns, FP32 and BF16."""
 import numpy as np
 import pytest
 import torch
@@ -68,3 +74,28 @@ def test_c3_forward_backward_in_one_graph(F):
     for a, b in zip(gw, gw_e):
         assert torch.equal(a, b)
     assert F.fcfs_device_status(clear=True) == 0
+
+
+@pytest.mark.parametrize("dtype", (torch.float32, torch.bfloat16))
+def test_c2_benchmark_step_graph_matches_oracle(F, orc, dtype):
+    import bench
+
+    replay, x, outs, axes = bench.c2_step(F, inputs, torch.device("cuda", 0), dtype, 16, tune=True, graph=True)
+    F.fcfs_clear_plans()  # the graph keeps the tuned launches; later tests use the default tiles
+    for y in outs.values():
+        y.fill_(float("nan"))
+    replay()
+    replay()  # a second replay overwrites the first with the same values
+    torch.cuda.synchronize()
+    assert F.fcfs_device_status(clear=True) == 0
+    xh = x.double().cpu().numpy()
+    scale = float(np.abs(xh).max())
+    for name, (r, s), m in bench.OPS:
+        y = outs[name]
+        idx = bench.sample_idx(tuple(y.shape), 100_000, 13)
+        want = orc.resize_at(xh, [dict(r=r, s=s, method=m)] * 2, idx)
+        got = bench.gather(y, idx)
+        if m == 0:  # nearest: an exact copy
+            assert np.array_equal(got, want)
+        else:
+            assert np.abs(got - want).max() <= (2e-6 if dtype == torch.float32 else 1e-2) * scale

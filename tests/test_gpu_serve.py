@@ -135,5 +135,32 @@ def test_rejections_timeouts_and_bad_requests(F):
         assert sv.stats()["completed"] == 40
 
 
+def test_output_dtype_must_match_the_server(F):
+    # the grouped kernel stores every slot in the server's out_dtype, so a request whose
+    # output has another dtype is refused on the host before anything is queued (a BF16
+    # buffer given to an FP32 server would otherwise receive stores twice its size)
+    import ctypes
+
+    from paper_2203_10670_gb300 import _native as N
+
+    x = inputs.uint8_pixels((1, 3, 48, 64), 9, device="cuda")
+    axes = [F.Axis(3, 2, F.BILINEAR)] * 2
+    for server_dtype, other in ((torch.float32, torch.bfloat16), (torch.bfloat16, torch.float32)):
+        with F.Server(64 << 20, out_dtype=server_dtype, max_inflight=4) as sv:
+            y = torch.zeros(F.out_shape(x.shape, axes), device="cuda", dtype=other)
+            with pytest.raises(F.FCFSError) as e:
+                sv.submit(x, (3, 2), F.BILINEAR, y=y)
+            assert e.value.status == N.FCFS_ERR_ARG
+            d = F.make_desc(x.shape, axes, N.FCFS_U8, N.FCFS_BF16 if other == torch.bfloat16 else N.FCFS_F32)
+            rid = ctypes.c_ulonglong()
+            for yp in (None, y.data_ptr()):  # pooled and caller-placed outputs alike
+                rc = sv._lib.fcfs_serve_submit(sv._h, ctypes.byref(d), x.data_ptr(), yp, 0.0, ctypes.byref(rid))
+                assert rc == N.FCFS_ERR_ARG
+            st = sv.stats()
+            assert st["submitted"] == 0 and st["steps"] == 0
+            torch.cuda.synchronize()
+            assert int(torch.count_nonzero(y.float())) == 0  # nothing was written
+
+
 def test_device_status_clean_after_serving(F):
     assert F.fcfs_device_status(clear=True) == 0

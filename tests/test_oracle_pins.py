@@ -4,7 +4,7 @@ Each test ties the oracle to a fact the paper or mathematics fixes:
   * the weight examples printed in Sec. 5.2 (golden fixture),
   * closed-form properties of the bilinear and Keys (a = -1/2) kernels,
   * exact-rational brute force of linear and Catmull-Rom interpolation,
-  * the paper's own construction (pad -> strided conv -> pixelshuffle, Sec. 3.2
+  * the paper's own construction (pad -> strided conv -> pixelshuffle, Sec. 3.1
     and Sec. 4) composed from PyTorch CPU library ops in float64,
   * scipy's linear interpolation at the same sample positions,
   * invariants (constants, ramps, identity, unreduced ratios, separability),
@@ -167,7 +167,7 @@ def test_printed_bicubic_matrices_are_not_keys(orc):
 # ------------------------------------------- exact-rational brute force (P7)
 
 def _ext(q, n, pad):
-    """Sec. 3.1 padding rules restated: replicate, constant (None), reflect about the edge samples."""
+    """Sec. 3 padding rules restated: replicate, constant (None), reflect about the edge samples."""
     if 0 <= q < n:
         return q
     if pad == CONST:
@@ -269,7 +269,7 @@ def test_bruteforce_2d_3d(orc, method, pad):
 # ------------------------------------- the paper's construction (P4), torch FP64
 
 def _construction(x, axes, pad, c):
-    """Sec. 3.2 / Sec. 4 pseudocode with library ops: pad, N-d conv with prod(r) output
+    """Sec. 3.1 / Sec. 4 pseudocode with library ops: pad, N-d conv with prod(r) output
     channels per input channel and stride s, N-d pixelshuffle (last axis fastest), crop."""
     import torch
     import torch.nn.functional as F
@@ -523,6 +523,31 @@ def test_adjoint_gather_equals_scatter(orc, pad):
     full = orc.adjoint_dx(g, spatial, axes, pad=pad)
     at = orc.adjoint_dx_at(g, spatial, axes, np.arange(full.size), pad=pad)
     assert np.max(np.abs(at - full.ravel())) <= 1e-13
+
+
+@pytest.mark.parametrize("spatial,ratios", [((29,), [(7, 5)]), ((9, 11), [(5, 4), (2, 3)]),
+                                            ((6, 7, 5), [(3, 2), (4, 3), (1, 2)])])
+@pytest.mark.parametrize("pad", (REPL, CONST, REFL))
+def test_resize_at_decodes_flat_indices(orc, spatial, ratios, pad):
+    # the sampled full-size GPU parity rests on resize_at; it must return exactly the
+    # entries of the full result at the flat indices of [n][c][out...] (plane, channel of
+    # the per-channel weights, each spatial output index), for every evaluation form
+    rng = np.random.default_rng(29)
+    n, C = 3, 4
+    x = rng.standard_normal((n, C) + spatial)
+    forms = [(_learnable_axes(rng, C, ratios), True)]
+    for m in METHODS:
+        for align in (0, 1, 2):
+            forms.append(([dict(r=r, s=s, method=m, align=align) for r, s in ratios], False))
+    forms.append(([dict(r=r, s=s, method=BICUBIC, cubic_a=-0.75) for r, s in ratios], False))
+    forms.append(([dict(r=r, s=s, method=BILINEAR) for r, s in ratios], True))
+    for axes, poly in forms:
+        full = orc.resize(x, axes, pad=pad, pad_value=0.25, polyphase=poly)
+        idx = np.concatenate([rng.integers(0, full.size, 300), [0, full.size - 1]])
+        at = orc.resize_at(x, axes, idx, pad=pad, pad_value=0.25, polyphase=poly)
+        assert np.array_equal(at, full.ravel()[idx])
+        # the decode is not a no-op: outputs of other planes / channels differ
+        assert not np.array_equal(at, full.ravel()[(idx + full[0, 0].size) % full.size])
 
 
 def _fd_slice(orc):
