@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(512) fcfs_bwd_dx2d(const __grid_constant__ Bwd
     float* sG = sWy + AY.r * NT;
     float* sF = sG + P.GRcap * P.GCp;
 
-    const int qx0 = tx * P.QX, qy0 = ty * P.QY;
-    const int nqx = min(P.QX, AX.n_in - qx0), nqy = min(P.QY, AY.n_in - qy0);
+    const int qx0 = P.rqx0 + tx * P.QX, qy0 = P.rqy0 + ty * P.QY;
+    const int nqx = min(P.QX, P.rqx1 - qx0), nqy = min(P.QY, P.rqy1 - qy0);
     const WinRange wx = win_range(AX, P.adj[2], P.pad, qx0, qx0 + nqx - 1);
     const WinRange wy = win_range(AY, P.adj[1], P.pad, qy0, qy0 + nqy - 1);
 

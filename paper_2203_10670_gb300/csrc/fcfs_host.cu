@@ -355,8 +355,9 @@ int fcfs_device_status(int clear) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
     const int v = read_status_fwd_tma(clear), w = read_status_bwd_tma(clear), u = read_status_fused_tc(clear);
-    if (v < 0 || w < 0 || u < 0) return fail(FCFS_ERR_CUDA, "reading the device status word failed");
-    return v | w | u;
+    const int p = read_status_psk(clear), q = read_status_psk_bf16(clear);
+    if (v < 0 || w < 0 || u < 0 || p < 0 || q < 0) return fail(FCFS_ERR_CUDA, "reading the device status word failed");
+    return v | w | u | p | q;
 }
 
 int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out) {
@@ -457,6 +458,11 @@ int forward_planned(const fcfs_desc* d, const void* x, void* y, const Epi* epi, 
     if (epi) P.epi = *epi;
     TileChoice tc;
     const bool have = get_plan(P, d->ndim, d->dtype_in, d->dtype_out, &tc);
+    if ((have && tc.psk == 1) || psk_policy() == 2) {
+        rc = psk_forward(d, P, st);
+        if (rc != -1) return rc;
+        clear_error();
+    }
     if (!have) {
         const bool use_tma = tma_eligible(d, x);
         tc = use_tma ? default_tma_tiles(P, dtype_size(d->dtype_in), d->ndim == 3) : default_tiles(P, d->ndim == 3);
@@ -544,11 +550,13 @@ int build_adjoint(const AxisP& A, AdjAxis* J) {
     return FCFS_OK;
 }
 
-// Largest g extent (windows * r) any input tile of width Q needs on one axis.
-static int g_capacity(const AxisP& A, const AdjAxis& J, int pad, int Q) {
+// Largest g extent (windows * r) any input tile of width Q needs on one axis,
+// over the tiles of the real indices [qa, qb) (qb < 0: the whole axis).
+static int g_capacity(const AxisP& A, const AdjAxis& J, int pad, int Q, int qa = 0, int qb = -1) {
+    if (qb < 0) qb = A.n_in;
     int cap = 0;
-    for (int q0 = 0; q0 < A.n_in; q0 += Q) {
-        const int q1 = std::min(A.n_in, q0 + Q) - 1;
+    for (int q0 = qa; q0 < qb; q0 += Q) {
+        const int q1 = std::min(qb, q0 + Q) - 1;
         const WinRange w = win_range(A, J, pad, q0, q1);
         cap = std::max(cap, (w.ihi - w.ilo + 1) * A.r);
     }
@@ -594,6 +602,10 @@ void plan_dx(BwdParams& B, bool is3d) {
     }
     B.qtiles_x = (AX.n_in + B.QX - 1) / B.QX;
     B.qtiles_y = (AY.n_in + B.QY - 1) / B.QY;
+    B.rqx0 = 0;
+    B.rqx1 = AX.n_in;
+    B.rqy0 = 0;
+    B.rqy1 = AY.n_in;
     if (is3d) {
         const long long base = (long long)B.qtiles_x * B.qtiles_y * B.planes;
         const long long chunks = std::max(1LL, (152LL * 6 + base - 1) / base);
@@ -603,6 +615,23 @@ void plan_dx(BwdParams& B, bool is3d) {
         B.QD = 1;
         B.qtiles_d = 1;
     }
+}
+
+// Restrict a planned 2D gather input gradient to the real indices
+// [x0, x1) x [y0, y1): tile counts and g capacities of that region's tiles.
+void plan_dx_region(BwdParams& B, int x0, int x1, int y0, int y1) {
+    B.rqx0 = x0;
+    B.rqx1 = x1;
+    B.rqy0 = y0;
+    B.rqy1 = y1;
+    B.QX = std::min(B.QX, std::max(32, (x1 - x0 + 31) / 32 * 32));
+    B.Gq = std::max(1, 256 / B.QX);
+    B.QY = std::min(B.QY, std::max(1, y1 - y0));
+    B.GCcap = g_capacity(B.ax[2], B.adj[2], B.pad, B.QX, x0, x1);
+    B.GRcap = g_capacity(B.ax[1], B.adj[1], B.pad, B.QY, y0, y1);
+    B.GCp = B.GCcap;
+    B.qtiles_x = (x1 - x0 + B.QX - 1) / B.QX;
+    B.qtiles_y = (y1 - y0 + B.QY - 1) / B.QY;
 }
 
 void plan_dw(BwdParams& B) {
@@ -1160,7 +1189,17 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
     if (gx && !is3d) {
         TmaDxParams T;
         int ntd = 0;
-        if (plan_dx_tma(d, B, gy, gx, &T, &ntd) == FCFS_OK) {
+        const bool tile_ok = plan_dx_tma(d, B, gy, gx, &T, &ntd) == FCFS_OK;
+        clear_error();
+        // the strip kernel on the interior and the gather kernel on the border bands, where the
+        // tile path has no register-blocked kernel for this window shape (or when asked for)
+        if (psk_policy() == 2 || (psk_policy() == 1 && !(tile_ok && T.rs_span > 0))) {
+            rc = psk_input_gradient(d, B, gy, gx, ntk, st);
+            if (rc == FCFS_OK) gx = nullptr;
+            else if (rc != -1) return rc;
+            clear_error();
+        }
+        if (gx && tile_ok) {
             cudaError_t e = cudaErrorInvalidValue;
             if (T.rs_span > 0) e = launch_dx_rs(T, d->dtype_out, st);
             if (e == cudaErrorInvalidValue) e = launch_dx_tma(T, ntd, d->dtype_out, d->dtype_in, st);
@@ -1406,6 +1445,11 @@ int prepare_tma3(const fcfs_desc* d, const FwdParams& P, TmaFwd3Params* T, int t
 // when the choice asks for it and the layout allows, else the gather kernel.
 int launch_choice(const fcfs_desc* d, FwdParams& P, int ntk, const TileChoice& t, cudaStream_t st) {
     const bool is3d = d->ndim == 3;
+    if (t.psk == 1) {
+        const int rc = psk_forward(d, P, st);
+        if (rc != -1) return rc;
+        clear_error();
+    }
     if (t.tma == 1 && is3d && tma_eligible(d, P.x)) {
         apply_tiles(P, true, t.WX, t.WY, t.WD, 0);
         TmaFwd3Params T;

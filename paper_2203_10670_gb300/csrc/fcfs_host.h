@@ -13,6 +13,7 @@ struct TileChoice {
     int tma = -1;    // 1: TMA-staged persistent kernel, 0: gather kernel, -1: best available
     int threads = 0; // CTA size of the TMA-staged kernel (0: 256)
     int rs = 1;      // 1: register-blocked variant when one is compiled for (r, span), 0: per-output kernel
+    int psk = 0;     // 1: polyphase strip kernel when the descriptor is in its scope (2D), 0: tile kernels
 };
 
 int fail(int status, const char* fmt, ...);
@@ -54,6 +55,16 @@ bool forward_has_epilogue_path(const fcfs_desc* d, const void* x);
 int fused_forward_tc(const fcfs_desc* d, const fcfs_epilogue* e, const void* x, void* y, cudaStream_t st);
 int read_status_fused_tc(int clear);
 int build_adjoint(const AxisP& A, AdjAxis* J);
+int build_adjp(const AxisP& A, AdjP* J);
+void plan_dx(BwdParams& B, bool is3d);
+void plan_dx_region(BwdParams& B, int x0, int x1, int y0, int y1);
+
+// polyphase strip kernels (fcfs_psk_host.cu): FCFS_OK when launched, -1 when the
+// descriptor is outside their scope (the caller takes another kernel), else an error
+int psk_forward(const fcfs_desc* d, const FwdParams& F, cudaStream_t st);
+int psk_input_gradient(const fcfs_desc* d, const BwdParams& B, const void* gy, void* gx, int ntk, cudaStream_t st);
+bool psk_enabled();
+int psk_policy();  // 0 never, 1 default, 2 wherever in scope
 
 // non-separable 2D kernels (fcfs_full2d.cu)
 int full2d_forward(const fcfs_desc* d, const void* x, void* y, cudaStream_t st);

@@ -111,6 +111,7 @@ struct BwdParams {
     int GRcap, GCcap, GDcap; // g tile capacity (rows, cols, depth planes)
     int GCp;                 // g tile pitch
     int Gq;                  // thread groups: blockDim = QX * Gq
+    int rqx0, rqx1, rqy0, rqy1;  // 2D gather kernel: real indices [rqx0, rqx1) x [rqy0, rqy1) it computes
     // weight-gradient tiling (output tiles as the forward)
     FwdParams fw;
     int dw_axis_off[3];      // offset of each axis's partials in a CTA record (floats)
@@ -417,6 +418,8 @@ size_t forward_smem_bytes(const FwdParams& P, bool is3d);
 size_t dx_smem_bytes(const BwdParams& P, bool is3d);
 size_t dw_smem_bytes(const BwdParams& P);
 cudaError_t launch_dx(const BwdParams& P, int nt, int dg, int dx, bool is3d, cudaStream_t st);
+int read_status_psk(int clear);
+int read_status_psk_bf16(int clear);
 cudaError_t launch_dw(const BwdParams& P, int nt, int din, int dg, cudaStream_t st);
 cudaError_t launch_dw_reduce(const BwdParams& P, cudaStream_t st);
 

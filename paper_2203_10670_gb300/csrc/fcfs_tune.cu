@@ -36,6 +36,15 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     std::vector<TileChoice> cands;
     TileChoice def = tma ? default_tma_tiles(P0, dtype_size(d->dtype_in), is3d) : default_tiles(P0, is3d);
     def.tma = tma ? 1 : 0;
+    def.psk = 0;
+    {
+        // the polyphase strip kernel, when the descriptor is in its scope
+        FwdParams P = P0;
+        TileChoice s = def;
+        s.psk = 1;
+        if (psk_enabled() && psk_forward(d, P, st) == FCFS_OK) cands.push_back(s);
+        clear_error();
+    }
     cands.push_back(def);
     const int ox_targets[] = {64, 128, 192, 256};
     const int oy_targets[] = {8, 16, 32, 48, 64};
@@ -53,6 +62,7 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
                     t.G = tma ? 0 : (gm == 0 ? def.G : (def.G == ry ? 1 : ry));
                     t.threads = tma ? ((gm & 1) == 0 ? 256 : 512) : 0;
                     t.rs = gm < 2 ? 1 : 0;
+                    t.psk = 0;
                     if (!tma && gm >= 2) continue;
                     FwdParams P = P0;
                     apply_tiles(P, is3d, t.WX, t.WY, t.WD, t.G);
