@@ -46,7 +46,8 @@ ALIGN_PAPER, ALIGN_HALF_PIXEL, ALIGN_FLOOR = 0, 1, 2
 class _Axis(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int), ("s", ctypes.c_int), ("method", ctypes.c_int),
                 ("K", ctypes.c_int), ("w", ctypes.POINTER(ctypes.c_double)),
-                ("w_per_channel", ctypes.c_int), ("align", ctypes.c_int), ("cubic_a", ctypes.c_double)]
+                ("w_per_channel", ctypes.c_int), ("align", ctypes.c_int), ("cubic_a", ctypes.c_double),
+                ("antialias", ctypes.c_int)]
 
 
 def lib():
@@ -127,7 +128,7 @@ def make_weights(method: int, r: int, s: int, K: int = 0):
 
 def _axes(axes, keep):
     """axes: list of dicts {r, s, method, K=0, w=None (array [C or 1][r][T] or [r][T]),
-    align=ALIGN_PAPER, cubic_a=0 (-1/2)}."""
+    align=ALIGN_PAPER, cubic_a=0 (-1/2), antialias=0 (1: widened kernel when s > r)}."""
     arr = (_Axis * len(axes))()
     for k, a in enumerate(axes):
         w = a.get("w")
@@ -136,6 +137,7 @@ def _axes(axes, keep):
         arr[k].K = a.get("K", 0)
         arr[k].align = a.get("align", ALIGN_PAPER)
         arr[k].cubic_a = float(a.get("cubic_a", 0.0))
+        arr[k].antialias = int(a.get("antialias", 0))
         if w is not None:
             w = np.ascontiguousarray(w, dtype=np.float64)
             keep.append(w)

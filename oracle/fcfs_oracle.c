@@ -25,6 +25,12 @@
  *       half-pixel centres p = (o + 1/2) s / r - 1/2, nearest x~[floor((o + 1/2) s / r)]
  *       floor nearest x~[floor(o s / r)] (linear/cubic as the paper's p)
  *     and the Keys parameter a (the paper's kernel has a = -1/2).
+ *   - antialiased downscale (not the paper's: the paper's kernels keep their
+ *     width when s > r), fixed bilinear / bicubic only, when s > r: output o
+ *     with sample position p takes every input t with |t - p| < R s / r
+ *     (R = 1 bilinear, 2 bicubic) with weight k((t - p) r / s), the weights
+ *     divided by their sum.  The kernel stretched by s / r is the low-pass
+ *     prefilter of common resize libraries' antialias mode.
  *   - polyphase form with explicit weights W[j][m]:
  *     y[i r + j] = sum_m W[j][m] x~[i s - L + m]            [Sec. 3.1 pseudocode: pad, conv(stride s, r outputs), pixelshuffle]
  *     window half width K >= K_min, T = 2K + 1, L = K - floor(s/2)
@@ -56,6 +62,7 @@ typedef struct {
     int w_per_channel;
     int align;        /* ORC_ALIGN_*: sample positions of the fixed methods */
     double cubic_a;   /* Keys parameter of bicubic; 0 -> -1/2 */
+    int antialias;    /* 1: widened, renormalised kernel when s > r (bilinear / bicubic) */
 } orc_axis;
 
 int orc_num_threads(void) {
@@ -148,11 +155,14 @@ typedef struct {
     int r, s, method, K, T, L, per_channel;
     int align;       /* ORC_ALIGN_* (fixed methods) */
     double cubic_a;  /* Keys parameter */
+    int antialias;   /* the widened kernel applies (s > r, bilinear or bicubic) */
     const double* w; /* polyphase weights (may be the method table) */
 } axis_t;
 
-/* the fixed-method table of this axis describes it exactly (paper alignment, a = -1/2) */
-static int table_exact(const axis_t* A) { return A->align == ORC_ALIGN_PAPER && A->cubic_a == -0.5; }
+/* the fixed-method table of this axis describes it exactly (paper alignment, a = -1/2, no antialias) */
+static int table_exact(const axis_t* A) {
+    return A->align == ORC_ALIGN_PAPER && A->cubic_a == -0.5 && !A->antialias;
+}
 
 #define MAXTAP 256
 
@@ -166,7 +176,7 @@ static int setup_axes(int ndim, const long long* in_shape, const orc_axis* ax, a
         if (a < lead) { /* identity axis of extent 1 */
             A->n_in = 1; A->r = 1; A->s = 1; A->method = ORC_NEAREST;
             A->K = 0; A->T = 1; A->L = 0; A->per_channel = 0;
-            A->align = ORC_ALIGN_PAPER; A->cubic_a = -0.5;
+            A->align = ORC_ALIGN_PAPER; A->cubic_a = -0.5; A->antialias = 0;
             tables[a] = (double*)malloc(sizeof(double));
             tables[a][0] = 1.0;
             A->w = tables[a];
@@ -182,6 +192,10 @@ static int setup_axes(int ndim, const long long* in_shape, const orc_axis* ax, a
             if (g->align < ORC_ALIGN_PAPER || g->align > ORC_ALIGN_FLOOR) return -1;
             A->align = g->align;
             A->cubic_a = g->cubic_a != 0.0 ? g->cubic_a : -0.5;
+            if (g->antialias != 0 && g->antialias != 1) return -1;
+            A->antialias = g->antialias && !g->w && g->method != ORC_NEAREST && g->s > g->r;
+            /* taps of a widened window: fewer than 2 R (s / r + 1) + 3 */
+            if (A->antialias && 2LL * orc_support(g->method) * (g->s / g->r + 1) + 3 > MAXTAP) return -1;
             if (g->w) {
                 A->w = g->w;
             } else {
@@ -222,6 +236,22 @@ static int taps_direct(const axis_t* A, long long o, long long* t, double* w) {
     int R = orc_support(A->method);
     long long b = orc_floor_div(num, den); /* floor(p) */
     int n = 0;
+    if (A->antialias) {
+        /* every q with |q - p| < R s / r, i.e. |q den - num| r < R s den (exact integers);
+         * weight k((q - p) r / s), then divided by the sum of the weights */
+        long long reach = (long long)R * ((A->s + A->r - 1) / A->r) + 1;
+        double sum = 0.0;
+        for (long long q = b - reach; q <= b + reach; ++q) {
+            long long d = q * den - num;
+            if ((d < 0 ? -d : d) * (long long)A->r >= (long long)R * A->s * den) continue;
+            t[n] = q;
+            w[n] = orc_kernel_a(A->method, (double)(d * A->r) / (double)(den * A->s), A->cubic_a);
+            sum += w[n];
+            ++n;
+        }
+        for (int k = 0; k < n; ++k) w[k] /= sum;
+        return n;
+    }
     for (long long q = b - R + 1; q <= b + R; ++q) {
         t[n] = q;
         w[n] = orc_kernel_a(A->method, (double)(num - q * den) / (double)den, A->cubic_a); /* k(p - q) */

@@ -50,7 +50,7 @@ __device__ __forceinline__ void sts_row(float* p, const float* h) {
 // 8-byte vectors (the lanes' loads contiguous, no conflicts) and only its
 // SPAN samples enter the sums.
 template <int R, int SPAN, typename Tin, typename Tout, int VW, bool XSPEC, bool XV>
-__global__ void __launch_bounds__(512) fcfs_fwd2d_rs(const __grid_constant__ TmaFwdParams T) {
+__global__ void __launch_bounds__(256, 3) fcfs_fwd2d_rs(const __grid_constant__ TmaFwdParams T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ TileGeo sgeo[2];
     __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
@@ -220,6 +220,7 @@ cudaError_t run_rs(const TmaFwdParams& T, cudaStream_t st) {
     const bool v4 = R * SPAN <= 36 && T.P.OX % 4 == 0 && no % 4 == 0 && y % (4 * sizeof(Tout)) == 0;
     const bool v2 = T.P.OX % 2 == 0 && no % 2 == 0 && y % (2 * sizeof(Tout)) == 0;
     if (!v2) return cudaErrorInvalidValue;
+    if (T.threads > 256) return cudaErrorInvalidValue;  // built for three 256-thread CTAs per SM
     // window per thread when lanes' windows (s_x samples apart) hit shared memory
     // banks at most two ways: odd s_x, or s_x samples within 8 bytes
     const int sx = T.P.ax[2].s;

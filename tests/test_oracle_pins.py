@@ -837,3 +837,80 @@ def test_fused_identity_mix_is_the_plain_layer(orc):
     perm = np.eye(4)[[2, 0, 3, 1]]
     assert np.allclose(orc.resize_fused(x, axes, mix=perm, pad=CONST, pad_value=0.25), z[:, [2, 0, 3, 1]],
                        rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------- antialiased downscale (f4)
+
+AA_RATIOS = [(2, 3), (1, 2), (3, 7), (2, 5), (3, 4)]
+
+
+@pytest.mark.parametrize("method,mode", [(BILINEAR, "bilinear"), (BICUBIC, "bicubic")])
+@pytest.mark.parametrize("pad,tpad", [(REPL, "replicate"), (REFL, "reflect"), (CONST, "constant")])
+def test_antialias_matches_library_on_padded_input(orc, method, mode, pad, tpad):
+    # float64 library interpolation with antialias=True at half-pixel centres equals the oracle's
+    # widened, renormalised kernel wherever the library's window stays inside its input; padding the
+    # input by M = m s pixels first (the library's own padding op) moves every output of the
+    # original image into that interior (output o -> o + m r), which pins the extension rule too.
+    # The library's antialiased bicubic uses the Keys constant a = -1/2.
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as TF
+
+    rng = np.random.default_rng(61 + method + 3 * pad)
+    x = rng.random((1, 2, 40, 53))
+    c = 0.3
+    R = 1 if method == BILINEAR else 2
+    for r, s in AA_RATIOS:
+        m = R + 2
+        M = m * s
+        xp = TF.pad(torch.from_numpy(x), (M, M, M, M), mode=tpad, **({"value": c} if tpad == "constant" else {}))
+        ref = TF.interpolate(xp, scale_factor=r / s, mode=mode, align_corners=False, antialias=True,
+                             recompute_scale_factor=False).numpy()
+        y = orc.resize(x, [dict(r=r, s=s, method=method, align=1, antialias=1)] * 2, pad=pad, pad_value=c)
+        Ho, Wo = y.shape[2:]
+        sub = ref[:, :, m * r:m * r + Ho, m * r:m * r + Wo]
+        assert np.abs(y - sub).max() <= 1e-13, (r, s)
+
+
+def test_antialias_closed_form_half_scale_bilinear(orc):
+    # paper alignment, 1/2: the hat stretched by 2 gives weights 1/4, 1/2, 1/4 at 2o - 1, 2o, 2o + 1
+    rng = np.random.default_rng(67)
+    x = rng.random((1, 1, 31))
+    y = orc.resize(x, [dict(r=1, s=2, method=BILINEAR, antialias=1)])[0, 0]
+    xe = np.concatenate([[x[0, 0, 0]], x[0, 0], [x[0, 0, -1]]])  # replicate one sample each side
+    want = 0.25 * xe[0:-2:2][:len(y)] + 0.5 * xe[1:-1:2][:len(y)] + 0.25 * xe[2::2][:len(y)]
+    assert np.abs(y - want).max() <= 1e-15
+
+
+@pytest.mark.parametrize("method", (BILINEAR, BICUBIC))
+@pytest.mark.parametrize("align", (0, 1))
+def test_antialias_invariants(orc, method, align):
+    rng = np.random.default_rng(71)
+    x = rng.random((1, 2, 23, 29))
+    for r, s in AA_RATIOS + [(3, 2), (4, 3), (1, 1), (5, 5)]:
+        ax = [dict(r=r, s=s, method=method, align=align, antialias=1)] * 2
+        # the weights of every output sum to one: constants are kept at every pad (the constant pad
+        # with the same value)
+        for pad in (REPL, CONST, REFL):
+            y = orc.resize(np.full_like(x, 0.7), ax, pad=pad, pad_value=0.7)
+            assert np.abs(y - 0.7).max() <= 1e-14
+        # no downscale (s <= r): the widened kernel is the plain one
+        plain = orc.resize(x, [dict(r=r, s=s, method=method, align=align)] * 2)
+        aa = orc.resize(x, ax)
+        if s <= r:
+            assert np.array_equal(plain, aa)
+        else:
+            assert not np.allclose(plain, aa)
+
+
+def test_antialias_adjoint_dot_product(orc):
+    rng = np.random.default_rng(73)
+    for method in (BILINEAR, BICUBIC):
+        for r, s in AA_RATIOS:
+            ax = [dict(r=r, s=s, method=method, align=1, antialias=1)] * 2
+            for pad in (REPL, CONST, REFL):
+                x = rng.standard_normal((1, 2, 19, 26))
+                y = orc.resize(x, ax, pad=pad, pad_value=0.0)
+                g = rng.standard_normal(y.shape)
+                dx = orc.adjoint_dx(g, x.shape[2:], ax, pad=pad)
+                lhs, rhs = np.vdot(y, g), np.vdot(x, dx)
+                assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.abs(y).sum())
