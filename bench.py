@@ -406,9 +406,12 @@ def run_ours(args, rank, world, device):
     del x, outs, replay
     torch.cuda.empty_cache()
     if not args.no_extras:
-        ex_rows, serve, ex_detail = extras(fcfs, inputs, device, stream, peak, tune=not args.no_tune, checks=checks)
+        ex_rows, serve, ex_detail, qsum = extras(fcfs, inputs, device, stream, peak, tune=not args.no_tune,
+                                                 checks=checks)
         rows.update(ex_rows)
         line["serve"] = serve
+        # f4: min PSNR (dB) / SSIM of libfcfs against torch interpolate over the D6 factors and methods
+        line["quality"] = {k: [v["min_psnr_db"], v["min_ssim"]] for k, v in qsum.items()}
         detail.update(ex_detail)
     check_device_status(fcfs, "the extra measurements")
     roofline["ops"] = rows
@@ -571,6 +574,8 @@ def extras(fcfs, inputs, device, stream, peak, tune=True, checks=True):
         detail[f"f3_fused_x2_conv1x1_64_relu_{str(dt)[-4:]}"] = fused_times(fcfs, inputs, device, stream, peak, dtype=dt)
         torch.cuda.empty_cache()
     check_device_status(fcfs, "the non-separable and fused measurements")
+    _, qsum = d6_quality(fcfs, inputs, device)
+    detail["f4_quality"] = qsum
     sv = serve_bench(fcfs, inputs, device)
     detail.update(sv)
     serve = {"fields": ["sat_Gpix/s", "sat_req/s", "p50_ms@0.5", "p99_ms@0.5", "p99_ms@0.9"]}
@@ -578,7 +583,7 @@ def extras(fcfs, inputs, device, stream, peak, tune=True, checks=True):
         sat, half, nine = sv[f"serve_{tag}_saturation"], sv[f"serve_{tag}_rate0.5"], sv[f"serve_{tag}_rate0.9"]
         serve[tag] = [sig(sat["gpix_s"]), sig(sat["req_s"]), sig(half["p50_ms"], 3), sig(half["p99_ms"], 3),
                       sig(nine["p99_ms"], 3)]
-    return rows, serve, detail
+    return rows, serve, detail, qsum
 
 
 # FP32 FMA peak of the non-tensor path: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
@@ -701,11 +706,56 @@ D6_UP = [(3, 2), (5, 4), (4, 3), (2, 1), (5, 2), (27, 11)]
 D6_DOWN = [(2, 3), (4, 5), (3, 4), (1, 2), (2, 5), (2, 11)]
 
 
+D6_MODES = (("nearest", 0, 2), ("bilinear", 1, 1), ("bicubic", 2, 1))  # (name, method, matched alignment)
+
+
+def d6_quality(fcfs, inputs, device):
+    """The paper's second experiment without its dataset: a 1x3x1024^2 natural-spectrum image resized by
+    the D6 factors and methods, each libfcfs result compared with torch.nn.functional.interpolate by PSNR
+    and SSIM (data range 1).  Pairings: "paper" = the paper's layer (top-left samples, Keys a = -1/2,
+    nearest rounding half up) against the library's default resize, as the paper compared them;
+    "matched" = half-pixel centres, a = -3/4, floor nearest (the library's convention); "antialias" =
+    the antialiased downscale against interpolate(antialias=True) (a = -1/2), where its window fits."""
+    import torch.nn.functional as TF
+    from paper_2203_10670_gb300 import quality
+
+    x = inputs.natural_image((1, 3, 1024, 1024), 12, device=device)
+    rows = []
+    for r, s_ in D6_UP + D6_DOWN:
+        for name, m, al in D6_MODES:
+            ax = [fcfs.Axis(r, s_, m)] * 2
+            kw = {} if name == "nearest" else {"align_corners": False}
+            ref = TF.interpolate(x, scale_factor=r / s_, mode=name, recompute_scale_factor=False, **kw)
+            row = {"ratio": f"{r}/{s_}", "method": name}
+            for tag, args in (("paper", dict()), ("matched", dict(align=al, cubic_a=-0.75))):
+                y = fcfs.resize(x, ax, **args)
+                if tuple(y.shape) != tuple(ref.shape):
+                    break
+                row[tag] = [round(quality.psnr(y, ref), 2), round(quality.ssim(y, ref), 4)]
+            if s_ > r and name != "nearest":
+                try:
+                    y = fcfs.resize(x, ax, align=fcfs.ALIGN_HALF_PIXEL, antialias=True)
+                    refa = TF.interpolate(x, scale_factor=r / s_, mode=name, align_corners=False, antialias=True,
+                                          recompute_scale_factor=False)
+                    row["antialias"] = [round(quality.psnr(y, refa), 2), round(quality.ssim(y, refa), 4)]
+                except fcfs.FCFSError:
+                    row["antialias"] = None  # the widened window exceeds the kernel templates
+            rows.append(row)
+    summary = {}
+    for tag in ("paper", "matched", "antialias"):
+        vals = [q[tag] for q in rows if q.get(tag)]
+        if vals:
+            summary[tag] = {"min_psnr_db": min(v[0] for v in vals), "min_ssim": min(v[1] for v in vals),
+                            "cases": len(vals)}
+    return rows, summary
+
+
 def d6_only(args, device):
     """Context for the paper's runtime claim (Sec. 6: the layer about as fast as the framework's resize):
     a synthetic 1x3x1024x1024 FP32 image (the CelebA size), six up and six down factors, three methods;
     libfcfs against torch.nn.functional.interpolate with the same sample convention (half-pixel centres,
-    Keys a = -0.75 for bicubic, floor for nearest), both timed with CUDA events."""
+    Keys a = -0.75 for bicubic, floor for nearest), both timed with CUDA events; then the image-quality
+    comparison of the paper's second experiment (PSNR and SSIM, d6_quality)."""
     from paper_2203_10670_gb300 import build as B
 
     B.build()
@@ -730,8 +780,10 @@ def d6_only(args, device):
             rows.append({"ratio": f"{r}/{s_}", "method": name, "fcfs_ms": tf * 1e3, "interpolate_ms": tt * 1e3,
                          "max_abs_diff": float((y - ref).abs().max())})
     ratio = float(np.exp(np.mean([np.log(q["fcfs_ms"] / q["interpolate_ms"]) for q in rows])))
+    qrows, qsum = d6_quality(fcfs, inputs, device)
     print(json.dumps({"mode": "d6: 1x3x1024^2 fp32, 12 factors x 3 methods, fcfs vs torch interpolate",
-                      "geomean_time_ratio_fcfs_over_interpolate": ratio, "cases": rows}), flush=True)
+                      "geomean_time_ratio_fcfs_over_interpolate": ratio, "quality_summary": qsum,
+                      "cases": rows, "quality": qrows}), flush=True)
 
 
 def full2d_only(args, device):

@@ -125,7 +125,24 @@ typedef struct {
     const float* w2d;        /* DEVICE non-separable 2D kernels, NULL for the separable
                                 layer; see "Non-separable 2D kernels" below */
     int w2d_per_channel;     /* 1: w2d is [C][r_y][r_x][T_y][T_x], 0: [r_y][r_x][T_y][T_x] */
+    int antialias;           /* 1: antialiased downscale of the fixed bilinear / bicubic
+                                methods; see "Antialiased downscale" below.  0: the paper's kernels */
 } fcfs_desc;
+
+/*
+ * Antialiased downscale (antialias = 1; not the paper's: its kernels keep their
+ * width when s > r, so a downscale samples without a low-pass prefilter).  On
+ * every axis with s > r and a fixed bilinear or bicubic method, output o with
+ * sample position p (the axis's alignment) takes every input t with
+ * |t - p| < R s / r (R = 1 bilinear, 2 bicubic) with weight k((t - p) r / s),
+ * the weights divided by their sum, padding as for the plain layer.  It is the
+ * prefilter of common resize libraries' antialias mode (their bicubic uses
+ * a = -1/2, the paper's constant), still a period-r polyphase operator.  Axes
+ * with s <= r, nearest and learnable axes are unchanged.  The widened window
+ * may hold at most 9 taps per phase and r x taps <= 256 (bilinear down to
+ * 1/4, bicubic down to 1/2); wider ones fail with FCFS_ERR_UNSUPPORTED.
+ * fcfs_make_weights keeps the paper's table.
+ */
 
 /*
  * Non-separable 2D kernels (w2d != NULL): the 2D convolution of Sec. 4 with a

@@ -43,7 +43,8 @@ class fcfs_desc(ctypes.Structure):
                 ("in_shape", ctypes.c_longlong * 3), ("out_shape", ctypes.c_longlong * 3),
                 ("dtype_in", ctypes.c_int), ("dtype_out", ctypes.c_int), ("pad", ctypes.c_int),
                 ("pad_value", ctypes.c_float), ("align", ctypes.c_int), ("axis", fcfs_axis * 3),
-                ("cubic_a", ctypes.c_float), ("w2d", ctypes.c_void_p), ("w2d_per_channel", ctypes.c_int)]
+                ("cubic_a", ctypes.c_float), ("w2d", ctypes.c_void_p), ("w2d_per_channel", ctypes.c_int),
+                ("antialias", ctypes.c_int)]
 
 
 class fcfs_epilogue(ctypes.Structure):

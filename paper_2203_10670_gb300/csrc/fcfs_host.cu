@@ -76,7 +76,12 @@ int template_taps(int nt) {
 // (num - q den) / den for tap q.  Nearest rounds the paper's position half up,
 // the floor alignment's down, and takes floor((2 j s + s) / (2 r)) for
 // half-pixel centres.
-static void fixed_phase(int method, int r, int s, int j, int align, double ka, int* first, double* w, int* nt) {
+//
+// Antialiased downscale (aa and s > r): the kernel is stretched by s / r: tap
+// q counts when |q den - num| r < R s den (exact integers), with weight
+// k((q - p) r / s), and the phase's weights are divided by their sum.
+static void fixed_phase(int method, int r, int s, int j, int align, double ka, int aa, int* first, double* w,
+                        int* nt) {
     if (method == FCFS_NEAREST) {
         const long long js = (long long)j * s;
         if (align == FCFS_ALIGN_FLOOR) *first = (int)(js / r);
@@ -93,6 +98,23 @@ static void fixed_phase(int method, int r, int s, int j, int align, double ka, i
     }
     const long long b = floor_div(num, den);
     const int R = support_radius(method);
+    if (aa && s > r) {
+        const long long reach = (long long)R * ((s + r - 1) / r) + 1;
+        int n = 0;
+        double sum = 0.0;
+        *first = 0;
+        for (long long q = b - reach; q <= b + reach; ++q) {
+            const long long dq = q * den - num;
+            if ((dq < 0 ? -dq : dq) * (long long)r >= (long long)R * s * den) continue;
+            if (n == 0) *first = (int)q;
+            if (n < kMaxAATaps) w[n] = kernel_value(method, (double)(dq * r) / (double)(den * s), ka);
+            sum += n < kMaxAATaps ? w[n] : 0.0;
+            ++n;
+        }
+        *nt = n;
+        for (int t = 0; t < std::min(n, kMaxAATaps); ++t) w[t] /= sum;
+        return;
+    }
     *first = (int)(b - R + 1);
     *nt = 2 * R;
     for (int t = 0; t < 2 * R; ++t) {
@@ -129,6 +151,7 @@ int validate_desc(const fcfs_desc* d, bool output_dtype_check) {
     if (d->pad < FCFS_PAD_REPLICATE || d->pad > FCFS_PAD_REFLECT) return fail(FCFS_ERR_ARG, "unknown pad mode %d", d->pad);
     if (d->align < FCFS_ALIGN_PAPER || d->align > FCFS_ALIGN_FLOOR) return fail(FCFS_ERR_ARG, "unknown alignment %d", d->align);
     if (!std::isfinite(d->cubic_a)) return fail(FCFS_ERR_ARG, "cubic_a must be finite");
+    if (d->antialias != 0 && d->antialias != 1) return fail(FCFS_ERR_ARG, "antialias must be 0 or 1");
     if (d->c > INT_MAX) return fail(FCFS_ERR_ARG, "c too large");
     if (d->w2d) {
         if (d->ndim != 2) return fail(FCFS_ERR_ARG, "non-separable kernels (w2d) need ndim == 2 (got %d)", d->ndim);
@@ -145,6 +168,12 @@ int validate_desc(const fcfs_desc* d, bool output_dtype_check) {
         }
         int rc = validate_axis(ax, a);
         if (rc) return rc;
+        if (d->antialias && !ax.w && !d->w2d && ax.method != FCFS_NEAREST && ax.s > ax.r) {
+            const int nt = fixed_taps(ax.method, ax.r, ax.s, d->align, keys_a(d), 1);
+            if (nt > FCFS_MAX_TAPS || ax.r * nt > kMaxR * kMaxFixedTaps)
+                return fail(FCFS_ERR_UNSUPPORTED, "axis %d: antialiased %d/%d needs %d taps per phase (at most %d)", a,
+                            ax.r, ax.s, nt, FCFS_MAX_TAPS);
+        }
         if (d->in_shape[a] < 0 || d->in_shape[a] > INT_MAX / 2)
             return fail(FCFS_ERR_ARG, "axis %d: input extent %lld out of range", a, d->in_shape[a]);
         const long long no = out_len(d->in_shape[a], d->axis[a].r, d->axis[a].s);
@@ -172,7 +201,7 @@ int dtype_size(int dt) { return dt == FCFS_F32 ? 4 : dt == FCFS_BF16 ? 2 : 1; }
 
 // Fill the compact polyphase form of one real axis; nt_kernel is the
 // template width every phase is evaluated with (zero-padded taps).
-void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel, int align, double ka) {
+void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel, int align, double ka, int aa) {
     memset(A, 0, sizeof(*A));
     A->r = a.r;
     A->s = a.s;
@@ -191,14 +220,17 @@ void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kerne
         (void)C;
         return;
     }
-    int first[kMaxR];
-    double w[kMaxFixedTaps];
+    // phases may differ in tap count (antialias): every phase takes the largest, zero-padded
+    int first[kMaxR], cnt[kMaxR];
+    double w[kMaxR][kMaxAATaps];
     int lo = INT_MAX, nt = 1;
     for (int j = 0; j < a.r; ++j) {
-        fixed_phase(a.method, a.r, a.s, j, align, ka, &first[j], w, &nt);
+        fixed_phase(a.method, a.r, a.s, j, align, ka, aa, &first[j], w[j], &cnt[j]);
         lo = std::min(lo, first[j]);
-        for (int t = 0; t < nt; ++t) A->wf[j * nt + t] = (float)w[t];
+        nt = std::max(nt, cnt[j]);
     }
+    for (int j = 0; j < a.r; ++j)
+        for (int t = 0; t < nt; ++t) A->wf[j * nt + t] = t < cnt[j] ? (float)w[j][t] : 0.f;
     int span = 0;
     for (int j = 0; j < a.r; ++j) {
         A->off[j] = (short)(first[j] - lo);
@@ -209,9 +241,24 @@ void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kerne
     A->span = span;
 }
 
-int axis_taps(const fcfs_axis& a) {
-    if (a.w) return 2 * (a.K ? a.K : k_min(a.method, a.s)) + 1;
-    return a.method == FCFS_NEAREST ? 1 : 2 * support_radius(a.method);
+// Taps per phase of the fixed table of an axis (the widest phase when antialiased).
+int fixed_taps(int method, int r, int s, int align, double ka, int aa) {
+    if (method == FCFS_NEAREST) return 1;
+    if (!(aa && s > r)) return 2 * support_radius(method);
+    int nt = 1;
+    for (int j = 0; j < r; ++j) {
+        int first, n;
+        double w[kMaxAATaps];
+        fixed_phase(method, r, s, j, align, ka, aa, &first, w, &n);
+        nt = std::max(nt, n);
+    }
+    return nt;
+}
+
+int axis_taps(const fcfs_desc* d, int a) {
+    const fcfs_axis& ax = d->axis[a];
+    if (ax.w) return 2 * (ax.K ? ax.K : k_min(ax.method, ax.s)) + 1;
+    return fixed_taps(ax.method, ax.r, ax.s, d->align, keys_a(d), d->w2d ? 0 : d->antialias);
 }
 
 void identity_axis(AxisP* A, int nt_kernel) {
@@ -373,8 +420,8 @@ int fcfs_make_weights(int method, int r, int s, int K, float* w_out, int* K_out)
     const int T = 2 * K + 1, L = K - s / 2;
     for (int j = 0; j < r; ++j) {
         int first, nt;
-        double w[kMaxFixedTaps];
-        fixed_phase(method, r, s, j, FCFS_ALIGN_PAPER, -0.5, &first, w, &nt);
+        double w[kMaxAATaps];
+        fixed_phase(method, r, s, j, FCFS_ALIGN_PAPER, -0.5, 0, &first, w, &nt);
         for (int m = 0; m < T; ++m) w_out[j * T + m] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const int m = first + t + L;  // tap offset first+t from i*s, window origin i*s - L
@@ -482,7 +529,7 @@ bool forward_has_epilogue_path(const fcfs_desc* d, const void* x) {
 
 int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* out, int* ntk) {
     int nt = 1;
-    for (int a = 0; a < d->ndim; ++a) nt = std::max(nt, axis_taps(d->axis[a]));
+    for (int a = 0; a < d->ndim; ++a) nt = std::max(nt, axis_taps(d, a));
     const int w = template_taps(nt);
     if (w < 0) return fail(FCFS_ERR_UNSUPPORTED, "%d taps per phase exceed the kernel templates", nt);
     FwdParams& P = *out;
@@ -490,7 +537,8 @@ int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* 
     const int lead = 3 - d->ndim;
     for (int a = 0; a < 3; ++a) {
         if (a < lead) identity_axis(&P.ax[a], w);
-        else fill_axis(&P.ax[a], d->axis[a - lead], d->in_shape[a - lead], (int)d->c, w, d->align, keys_a(d));
+        else fill_axis(&P.ax[a], d->axis[a - lead], d->in_shape[a - lead], (int)d->c, w, d->align, keys_a(d),
+                       d->antialias);
     }
     P.planes = d->n * d->c;
     P.C = (int)d->c;

@@ -26,7 +26,8 @@ int support_radius(int method);
 int k_min(int method, int s);
 long long out_len(long long n, int r, int s);
 int template_taps(int nt);
-int axis_taps(const fcfs_axis& a);
+int axis_taps(const fcfs_desc* d, int a);
+int fixed_taps(int method, int r, int s, int align, double ka, int aa);
 
 int validate_axis(const fcfs_axis& a, int idx);
 int validate_desc(const fcfs_desc* d, bool output_dtype_check);
@@ -34,7 +35,7 @@ long long numel_in(const fcfs_desc* d);
 long long numel_out(const fcfs_desc* d);
 int dtype_size(int dt);
 
-void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel, int align, double ka);
+void fill_axis(AxisP* A, const fcfs_axis& a, long long n_in, int C, int nt_kernel, int align, double ka, int aa);
 void identity_axis(AxisP* A, int nt_kernel);
 
 int build_forward_params(const fcfs_desc* d, const void* x, void* y, FwdParams* out, int* ntk);

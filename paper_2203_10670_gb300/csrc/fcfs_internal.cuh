@@ -19,7 +19,8 @@
 namespace fcfs {
 
 constexpr int kMaxR = FCFS_MAX_R;   // phases per axis in the fixed tables
-constexpr int kMaxFixedTaps = 4;    // nearest 1, bilinear 2, bicubic 4
+constexpr int kMaxFixedTaps = 4;    // nearest 1, bilinear 2, bicubic 4 (the table holds kMaxR x 4 entries)
+constexpr int kMaxAATaps = 16;      // taps a widened (antialiased) phase may count on the host
 
 // One spatial axis in compact polyphase form.  Window i reads the input
 // positions [i*s + lo, i*s + lo + span); phase j uses the nt taps starting at
@@ -36,7 +37,7 @@ struct AxisP {
     const float* w;          // learnable [C or 1][r][nt_src]
     long long w_cstride;     // floats between channels (0 = shared)
     short off[kMaxR];        // per-phase first tap relative to lo
-    float wf[kMaxR * kMaxFixedTaps];  // fixed-method table [r][nt_src]
+    float wf[kMaxR * kMaxFixedTaps];  // fixed-method table [r][nt_src] (r * nt_src <= kMaxR * 4)
 };
 
 // Pointwise epilogue of the forward store (the bias and activation of the

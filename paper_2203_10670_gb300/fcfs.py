@@ -121,9 +121,9 @@ _DESC_CACHE_MAX = 256
 
 def make_desc(shape: Sequence[int], axes: Sequence[Axis], dtype_in: int, dtype_out: int,
               pad: int = PAD_REPLICATE, pad_value: float = 0.0, align: int = ALIGN_PAPER,
-              cubic_a: float = 0.0) -> N.fcfs_desc:
+              cubic_a: float = 0.0, antialias: bool = False) -> N.fcfs_desc:
     """Descriptor for an input of shape [n, c, *spatial] (spatial outermost first).
-    align / cubic_a: sample alignment and Keys parameter of the fixed methods
+    align / cubic_a / antialias: sample alignment, Keys parameter and antialiased downscale of the fixed methods
     (ALIGN_PAPER and 0 = the paper's -0.5 by default).
 
     Descriptors are cached by their arguments (a learnable axis by its weight
@@ -132,18 +132,18 @@ def make_desc(shape: Sequence[int], axes: Sequence[Axis], dtype_in: int, dtype_o
            tuple((a.r, a.s, a.method, a.K, None if a.w is None else (a.w.data_ptr(), tuple(a.w.shape), a.w.dtype,
                                                                       a.w.is_cuda, a.w.is_contiguous()))
                  for a in axes),
-           dtype_in, dtype_out, pad, float(pad_value), int(align), float(cubic_a))
+           dtype_in, dtype_out, pad, float(pad_value), int(align), float(cubic_a), int(bool(antialias)))
     hit = _DESC_CACHE.get(key)
     if hit is not None:
         return N.fcfs_desc.from_buffer_copy(hit)
-    d = _build_desc(shape, axes, dtype_in, dtype_out, pad, pad_value, align, cubic_a)
+    d = _build_desc(shape, axes, dtype_in, dtype_out, pad, pad_value, align, cubic_a, antialias)
     if len(_DESC_CACHE) >= _DESC_CACHE_MAX:
         _DESC_CACHE.clear()
     _DESC_CACHE[key] = N.fcfs_desc.from_buffer_copy(d)
     return d
 
 
-def _build_desc(shape, axes, dtype_in, dtype_out, pad, pad_value, align, cubic_a) -> N.fcfs_desc:
+def _build_desc(shape, axes, dtype_in, dtype_out, pad, pad_value, align, cubic_a, antialias=False) -> N.fcfs_desc:
     nd = len(shape) - 2
     if nd != len(axes) or not 1 <= nd <= 3:
         raise ValueError(f"{len(axes)} axes for a tensor with {nd} spatial dims")
@@ -174,6 +174,7 @@ def _build_desc(shape, axes, dtype_in, dtype_out, pad, pad_value, align, cubic_a
     d.pad, d.pad_value = pad, float(pad_value)
     d.align = int(align)
     d.cubic_a = float(cubic_a)
+    d.antialias = 1 if antialias else 0
     return d
 
 
@@ -189,7 +190,7 @@ def _stream(device) -> int:
 
 def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_value: float = 0.0,
            out_dtype: Optional[torch.dtype] = None, out: Optional[torch.Tensor] = None, align: int = ALIGN_PAPER,
-           cubic_a: float = 0.0) -> torch.Tensor:
+           cubic_a: float = 0.0, antialias: bool = False) -> torch.Tensor:
     """y = FCFS(x) for x [n, c, *spatial] (float32, bfloat16 or uint8).
 
     A CUDA tensor is processed on its device and current stream.  A host tensor
@@ -197,7 +198,8 @@ def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_
     back to host memory (pinned inputs make both copies asynchronous)."""
     if not x.is_cuda:
         dev = torch.device("cuda", torch.cuda.current_device())
-        y = resize(x.to(dev, non_blocking=True), axes, pad, pad_value, out_dtype, align=align, cubic_a=cubic_a)
+        y = resize(x.to(dev, non_blocking=True), axes, pad, pad_value, out_dtype, align=align, cubic_a=cubic_a,
+                   antialias=antialias)
         if out is not None:
             out.copy_(y)
             return out
@@ -205,7 +207,7 @@ def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_
     if out_dtype is None:
         out_dtype = torch.float32 if x.dtype == torch.uint8 else x.dtype
     x = x.contiguous()
-    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value, align, cubic_a)
+    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value, align, cubic_a, antialias)
     oshape = out_shape(x.shape, axes)
     if out is None:
         out = torch.empty(oshape, dtype=out_dtype, device=x.device)
@@ -217,14 +219,15 @@ def resize(x: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE, pad_
 
 def resize_backward(x: Optional[torch.Tensor], gy: torch.Tensor, axes: Sequence[Axis], pad: int = PAD_REPLICATE,
                     pad_value: float = 0.0, in_shape=None, in_dtype=None, need_dx: bool = True,
-                    need_dw: Sequence[bool] = (), align: int = ALIGN_PAPER, cubic_a: float = 0.0):
+                    need_dw: Sequence[bool] = (), align: int = ALIGN_PAPER, cubic_a: float = 0.0,
+                    antialias: bool = False):
     """(gx, [gw per axis]) of the FCFS forward for upstream gradient gy."""
     if in_shape is None:
         in_shape = tuple(x.shape)
     if in_dtype is None:
         in_dtype = x.dtype
     gy = gy.contiguous()
-    d = make_desc(in_shape, axes, _DT[in_dtype], _DT[gy.dtype], pad, pad_value, align, cubic_a)
+    d = make_desc(in_shape, axes, _DT[in_dtype], _DT[gy.dtype], pad, pad_value, align, cubic_a, antialias)
     dev = gy.device
     gx = torch.empty(in_shape, dtype=in_dtype, device=dev) if need_dx else None
     gws, ptrs = [], []
@@ -251,7 +254,7 @@ class FCFSFunction(torch.autograd.Function):
     def forward(ctx, x, spec, *weights):
         axes = [Axis(a.r, a.s, a.method, a.K, w) for a, w in zip(spec["axes"], weights)]
         y = resize(x, axes, spec["pad"], spec["pad_value"], spec.get("out_dtype"), align=spec.get("align", ALIGN_PAPER),
-                   cubic_a=spec.get("cubic_a", 0.0))
+                   cubic_a=spec.get("cubic_a", 0.0), antialias=spec.get("antialias", False))
         ctx.spec = spec
         ctx.save_for_backward(x, *[w if w is not None else torch.empty(0) for w in weights])
         ctx.has_w = [w is not None for w in weights]
@@ -266,7 +269,8 @@ class FCFSFunction(torch.autograd.Function):
         gx, gws = resize_backward(x if any(need_w) else None, gy.to(spec.get("out_dtype") or x.dtype), axes,
                                   spec["pad"], spec["pad_value"], in_shape=tuple(x.shape), in_dtype=x.dtype,
                                   need_dx=ctx.needs_input_grad[0], need_dw=need_w,
-                                  align=spec.get("align", ALIGN_PAPER), cubic_a=spec.get("cubic_a", 0.0))
+                                  align=spec.get("align", ALIGN_PAPER), cubic_a=spec.get("cubic_a", 0.0),
+                                  antialias=spec.get("antialias", False))
         return (gx, None, *gws)
 
 
@@ -278,11 +282,12 @@ class FCFS(torch.nn.Module):
 
     def __init__(self, channels: int, ratios, method: int = BILINEAR, pad: int = PAD_REPLICATE,
                  pad_value: float = 0.0, learnable: bool = False, K: int = 0, out_dtype=None,
-                 align: int = ALIGN_PAPER, cubic_a: float = 0.0):
+                 align: int = ALIGN_PAPER, cubic_a: float = 0.0, antialias: bool = False):
         super().__init__()
         self.ratios = [tuple(rs) for rs in ratios]
         self.method, self.pad, self.pad_value, self.out_dtype = method, pad, pad_value, out_dtype
         self.align, self.cubic_a = align, cubic_a  # fixed-method sampling (learnable taps ignore it)
+        self.antialias = antialias
         self.weights = torch.nn.ParameterList()
         self.Ks = []
         for r, s in self.ratios:
@@ -295,7 +300,7 @@ class FCFS(torch.nn.Module):
     def forward(self, x):
         spec = {"axes": [Axis(r, s, self.method, k) for (r, s), k in zip(self.ratios, self.Ks)],
                 "pad": self.pad, "pad_value": self.pad_value, "out_dtype": self.out_dtype,
-                "align": self.align, "cubic_a": self.cubic_a}
+                "align": self.align, "cubic_a": self.cubic_a, "antialias": self.antialias}
         ws = [w.contiguous() for w in self.weights] if self.learnable else [None] * len(self.ratios)
         return FCFSFunction.apply(x, spec, *ws)
 
@@ -315,13 +320,14 @@ def resize_fused(x: torch.Tensor, axes: Sequence[Axis], mix: Optional[torch.Tens
                  bias: Optional[torch.Tensor] = None, act: int = ACT_NONE, alpha: float = 0.0, lo: float = 0.0,
                  hi: float = 0.0, pad: int = PAD_REPLICATE, pad_value: float = 0.0,
                  out_dtype: Optional[torch.dtype] = None, align: int = ALIGN_PAPER, cubic_a: float = 0.0,
+                 antialias: bool = False,
                  out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """y = act(mix @ FCFS(x) + bias) over channels, in one kernel (x [n, c, H, W] on a CUDA device;
     mix [c_out, c] float32 or None for the identity; bias [c_out] or None)."""
     if out_dtype is None:
         out_dtype = out.dtype if out is not None else torch.float32 if x.dtype == torch.uint8 else x.dtype
     x = x.contiguous()
-    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value, align, cubic_a)
+    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value, align, cubic_a, antialias)
     e = N.fcfs_epilogue()
     for name, t in (("mix", mix), ("bias", bias)):
         if t is not None and (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()):
@@ -490,11 +496,11 @@ class Server:
 
     def submit(self, x: torch.Tensor, ratio, method: int = BILINEAR, y: Optional[torch.Tensor] = None,
                arrival: Optional[float] = None, pad: int = PAD_REPLICATE, pad_value: float = 0.0,
-               align: int = ALIGN_PAPER, cubic_a: float = 0.0) -> int:
+               align: int = ALIGN_PAPER, cubic_a: float = 0.0, antialias: bool = False) -> int:
         r, s = ratio
         axes = [Axis(r, s, method)] * 2
         dout = _DT[y.dtype] if y is not None else _DT[self.out_dtype]
-        d = make_desc(x.shape, axes, _DT[x.dtype], dout, pad, pad_value, align, cubic_a)
+        d = make_desc(x.shape, axes, _DT[x.dtype], dout, pad, pad_value, align, cubic_a, antialias)
         rid = ctypes.c_ulonglong()
         t = self.clock() if arrival is None else float(arrival)
         check(self._lib.fcfs_serve_submit(self._h, ctypes.byref(d), x.data_ptr(),

@@ -14,6 +14,8 @@ Workloads (spatial axes outermost first):
       method uniform over nearest/bilinear/bicubic; Poisson arrivals (seed 5)
   c5  1x3x8192x8192 U[0,1) seed 6 (bicubic 7/5); 1x1x256x256x256 U[0,1)
       seed 7 (trilinear 3/2)
+  quality comparison (the paper's second experiment): 1x3x1024x1024 images
+      with a natural-image (1/f) spectrum, seed 12
 """
 from __future__ import annotations
 
@@ -47,6 +49,23 @@ def normal(shape, seed: int, device="cpu", dtype=torch.float32) -> torch.Tensor:
     """N(0, 1) drawn in float32; bf16 values are the round-to-nearest of those draws."""
     x = torch.randn(shape, generator=_gen(seed, device), device=device, dtype=torch.float32)
     return x if dtype == torch.float32 else x.to(dtype)
+
+
+def natural_image(shape, seed: int, device="cpu", dtype=torch.float32) -> torch.Tensor:
+    """Images [n, c, H, W] with the 1/f amplitude spectrum of natural photographs
+    (random phases from the seed), each plane scaled to [0, 1]: smooth regions and
+    edges at every scale, a stand-in for photographs such as face images."""
+    n, c, H, W = shape
+    g = torch.Generator().manual_seed(seed)
+    fy = torch.fft.fftfreq(H, dtype=torch.float64)[:, None]
+    fx = torch.fft.rfftfreq(W, dtype=torch.float64)[None, :]
+    f = torch.sqrt(fy * fy + fx * fx)
+    f[0, 0] = 1.0
+    phase = torch.rand((n, c, H, W // 2 + 1), generator=g, dtype=torch.float64) * (2 * math.pi)
+    img = torch.fft.irfft2(torch.polar(1.0 / f, phase), s=(H, W))
+    lo = img.amin(dim=(2, 3), keepdim=True)
+    hi = img.amax(dim=(2, 3), keepdim=True)
+    return ((img - lo) / (hi - lo)).to(device=device, dtype=dtype)
 
 
 def uint8_pixels(shape, seed: int, device="cpu") -> torch.Tensor:
