@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--fused", action="store_true",
                    help="time only the fused resize + 1x1 conv + ReLU decoder block (8x64x256^2, x2), "
                         "fused and unfused, in --dtype")
+    p.add_argument("--serve", action="store_true",
+                   help="time only the c4 serving loop (saturation and Poisson arrival rates, FP32 and BF16 outputs)")
     p.add_argument("--full2d", action="store_true",
                    help="time only the non-separable 5x5 learnable kernels on the c3 tensor (bf16, 5/4), "
                         "with --batch images: forward, input gradient, both gradients")
@@ -821,17 +823,26 @@ def serve_bench(fcfs, inputs, device, count=None, passes=3, repeats=3):
         out_bytes = [3 * (r["H"] * r["r"] // r["s"]) * (r["W"] * r["r"] // r["s"]) * (4 if code == 0 else 2)
                      for r in reqs]
 
+        xptrs = [base + int(o) for o in offs[:-1]]
+
         def run(rate, npass=1):
             with fcfs.Server(max(8 << 30, 64 * max(out_bytes)), max_inflight=64, out_dtype=odt,
                              tile_budget_per_step=8192, auto_release=True) as sv:
                 t0 = fcfs.Server.clock() + 0.01
-                for _ in range(npass):
-                    for k in range(count):
-                        due = t0 if rate is None else t0 + gaps[k] / rate
-                        if rate is not None:
-                            while fcfs.Server.clock() < due:
-                                pass
-                        sv.submit_raw(descs[k], base + int(offs[k]), None, due)
+                if rate is None:  # closed loop: everything arrives at t0, queued in batches
+                    for _ in range(npass):
+                        for k0 in range(0, count, 1024):
+                            k1 = min(count, k0 + 1024)
+                            sv.submit_batch_raw(descs[k0:k1], xptrs[k0:k1], None, [t0] * (k1 - k0))
+                else:  # open loop: every request whose arrival time has passed is queued in one call
+                    due = t0 + gaps / rate
+                    k = 0
+                    while k < count:
+                        now = fcfs.Server.clock()
+                        k1 = int(np.searchsorted(due, now, side="right"))
+                        if k1 > k:
+                            sv.submit_batch_raw(descs[k:k1], xptrs[k:k1], None, due[k:k1].tolist())
+                            k = k1
                 sv.drain(300_000)
                 return sv.stats()
 
@@ -938,6 +949,14 @@ def main():
             return
         if args.d6:
             d6_only(args, device)
+            return
+        if args.serve:
+            from paper_2203_10670_gb300 import build as B
+
+            B.build()
+            from paper_2203_10670_gb300 import fcfs, inputs
+
+            print(json.dumps({"mode": "c4 serving", **serve_bench(fcfs, inputs, device)}), flush=True)
             return
         run_ours(args, rank, world, device)
     finally:

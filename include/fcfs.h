@@ -240,8 +240,18 @@ int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, f
 int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, void* stream, int reps, float* best_ms,
                       int* n_candidates);
 
-/* Forget every plan fcfs_tune_forward stored (later calls use the default tiles). */
+/* Forget every plan fcfs_tune_forward stored (later calls use the default tiles).
+ * The on-disk cache (below) is left as it is and not read again in this process. */
 void fcfs_clear_plans(void);
+
+/*
+ * Number of plans in the process-wide cache.  With the environment variable
+ * FCFS_TUNE_CACHE naming a file, each plan fcfs_tune_forward chooses is
+ * appended to that file (one text line: the device kind it was measured on,
+ * the key, the tile), and the first plan lookup of a process loads the lines
+ * of the same device kind, so tuned shapes keep their tiles across runs.
+ */
+int fcfs_plan_count(void);
 
 /*
  * Status word written by the device code: 0 when every bounded wait of the
@@ -310,6 +320,7 @@ typedef struct {
     double bytes_moved;                     /* algorithmic input + output bytes */
     double wall_s;                          /* first arrival to last completion */
     double gpix_s, gbytes_s;
+    long long canceled;                     /* requests ended by fcfs_serve_cancel */
 } fcfs_serve_stats_t;
 
 /* Seconds on the steady clock the serving loop stamps latencies with. */
@@ -330,6 +341,16 @@ int fcfs_serve_create(const fcfs_serve_config* cfg, void* stream, void** handle)
 int fcfs_serve_submit(void* h, const fcfs_desc* d, const void* x, void* y, double arrival_s,
                       unsigned long long* req_id);
 
+/* Queue `count` requests at once (the same rules as fcfs_serve_submit for each):
+ * descs[k], xs[k], ys[k] (ys may be NULL: every output pooled), arrivals[k];
+ * ids[k] (may be NULL) receives each id.  Requests are validated in order and
+ * queued in one critical section; the first invalid one stops the batch: the
+ * requests before it are queued (*n_submitted of them, may be NULL) and its
+ * status is returned.  One call replaces a call per request for callers that
+ * receive requests in groups. */
+int fcfs_serve_submit_batch(void* h, int count, const fcfs_desc* descs, const void* const* xs, void* const* ys,
+                            const double* arrivals, unsigned long long* ids, int* n_submitted);
+
 /* Non-blocking: up to `max` ids of completed requests (each reported once).
  * Returns FCFS_OK, or the error that stopped the server. */
 int fcfs_serve_poll(void* h, unsigned long long* done_ids, int max, int* n_done);
@@ -339,6 +360,15 @@ int fcfs_serve_result(void* h, unsigned long long id, void** y);
 
 /* Return a completed request's pooled output to the pool (auto_release == 0). */
 int fcfs_serve_release(void* h, unsigned long long id);
+
+/* Cancel a request (a client that gives up on it).  Queued: it is removed at
+ * once.  Running: no further tile of it is launched; it ends when its launched
+ * tiles finish.  Either way its id is reported by fcfs_serve_poll like a
+ * completion, its output is left incomplete (pooled memory returns to the
+ * pool, fcfs_serve_result refuses it), and it is left out of the latency and
+ * throughput figures (counted in fcfs_serve_stats_t.canceled).  FCFS_ERR_ARG
+ * when the id is neither queued nor running. */
+int fcfs_serve_cancel(void* h, unsigned long long id);
 
 /* Wait until every queued request has completed, at most timeout_ms (-1: the
  * configured timeout); FCFS_ERR_TIMEOUT otherwise.  No GPU wait is unbounded. */

@@ -64,7 +64,7 @@ class fcfs_serve_stats_t(ctypes.Structure):
                 ("max_inflight_seen", ctypes.c_int), ("p50_ms", ctypes.c_double), ("p90_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("out_pixels", ctypes.c_double),
                 ("bytes_moved", ctypes.c_double), ("wall_s", ctypes.c_double), ("gpix_s", ctypes.c_double),
-                ("gbytes_s", ctypes.c_double)]
+                ("gbytes_s", ctypes.c_double), ("canceled", ctypes.c_longlong)]
 
 
 # every function include/fcfs.h declares: name -> (restype, argtypes)
@@ -83,13 +83,18 @@ SIGNATURES = {
     "fcfs_tune_forward": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P, _I, ctypes.POINTER(ctypes.c_float),
                                ctypes.POINTER(_I)]),
     "fcfs_clear_plans": (None, []),
+    "fcfs_plan_count": (_I, []),
     "fcfs_device_status": (_I, [_I]),
     "fcfs_backward_noalloc": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P, _P, _P]),
     "fcfs_serve_clock": (ctypes.c_double, []),
     "fcfs_serve_create": (_I, [ctypes.POINTER(fcfs_serve_config), _P, ctypes.POINTER(_P)]),
     "fcfs_serve_submit": (_I, [_P, ctypes.POINTER(fcfs_desc), _P, _P, ctypes.c_double,
                                ctypes.POINTER(ctypes.c_ulonglong)]),
+    "fcfs_serve_submit_batch": (_I, [_P, _I, ctypes.POINTER(fcfs_desc), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_ulonglong),
+                                     ctypes.POINTER(_I)]),
     "fcfs_serve_poll": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong), _I, ctypes.POINTER(_I)]),
+    "fcfs_serve_cancel": (_I, [_P, ctypes.c_ulonglong]),
     "fcfs_serve_result": (_I, [_P, ctypes.c_ulonglong, ctypes.POINTER(_P)]),
     "fcfs_serve_release": (_I, [_P, ctypes.c_ulonglong]),
     "fcfs_serve_drain": (_I, [_P, _I]),

@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if p.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if force or _stale(LIB, objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-ldl"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             sys.stderr.write(p.stdout + p.stderr)

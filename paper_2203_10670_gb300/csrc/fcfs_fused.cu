@@ -218,6 +218,7 @@ cudaError_t launch_fused_ob(const FusedParams& F, int ntk, int din, long long bl
 using namespace fcfs;
 
 extern "C" int fcfs_forward_fused(const fcfs_desc* d, const fcfs_epilogue* e, const void* x, void* y, void* stream) {
+    NvtxRange nv("fcfs_forward_fused");
     clear_error();
     int rc = validate_desc(d, true);
     if (rc) return rc;

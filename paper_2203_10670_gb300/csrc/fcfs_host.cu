@@ -288,6 +288,92 @@ struct PlanKeyHash {
 static std::mutex g_plan_mu;
 static std::unordered_map<PlanKey, TileChoice, PlanKeyHash> g_plans;
 
+// On-disk plan cache.  When FCFS_TUNE_CACHE names a file, every plan
+// fcfs_tune_forward chooses is appended to it as one text line
+//   fcfs-plan <device> <16 key integers> <8 tile integers>
+// and the first plan lookup of a process loads the lines measured on the same
+// kind of device (name, SM count and compute capability folded into <device>),
+// so a tuned shape keeps its tiles across processes without timing again.
+static std::once_flag g_cache_once;
+
+static unsigned long long device_signature() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return 0;
+    unsigned long long h = 1469598103934665603ull;
+    for (const char* c = prop.name; *c; ++c) h = (h ^ (unsigned char)*c) * 1099511628211ull;
+    h = (h ^ (unsigned long long)prop.multiProcessorCount) * 1099511628211ull;
+    h = (h ^ (unsigned long long)(prop.major * 100 + prop.minor)) * 1099511628211ull;
+    return h;
+}
+
+static void key_ints(const PlanKey& k, int* v) {
+    int n = 0;
+    v[n++] = k.ndim;
+    for (int a = 0; a < 3; ++a) v[n++] = k.r[a];
+    for (int a = 0; a < 3; ++a) v[n++] = k.s[a];
+    v[n++] = k.nt;
+    v[n++] = k.din;
+    v[n++] = k.dout;
+    for (int a = 0; a < 3; ++a) v[n++] = k.lo[a];
+    for (int a = 0; a < 3; ++a) v[n++] = k.span[a];
+}
+
+static void load_plan_cache() {
+    const char* path = getenv("FCFS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    const unsigned long long sig = device_signature();
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        unsigned long long dsig = 0;
+        int v[24], used = 0;
+        if (sscanf(line, "fcfs-plan %llu%n", &dsig, &used) != 1 || dsig != sig) continue;
+        const char* q = line + used;
+        int n = 0;
+        while (n < 24) {
+            int k = 0;
+            if (sscanf(q, "%d%n", &v[n], &k) != 1) break;
+            q += k;
+            ++n;
+        }
+        if (n != 24) continue;
+        PlanKey key;
+        memset(&key, 0, sizeof key);
+        int i = 0;
+        key.ndim = v[i++];
+        for (int a = 0; a < 3; ++a) key.r[a] = v[i++];
+        for (int a = 0; a < 3; ++a) key.s[a] = v[i++];
+        key.nt = v[i++];
+        key.din = v[i++];
+        key.dout = v[i++];
+        for (int a = 0; a < 3; ++a) key.lo[a] = v[i++];
+        for (int a = 0; a < 3; ++a) key.span[a] = v[i++];
+        TileChoice t{v[16], v[17], v[18]};
+        t.G = v[19];
+        t.tma = v[20];
+        t.threads = v[21];
+        t.rs = v[22];
+        t.psk = v[23];
+        g_plans[key] = t;
+    }
+    fclose(f);
+}
+
+static void save_plan(const PlanKey& k, const TileChoice& t) {
+    const char* path = getenv("FCFS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    int v[16];
+    key_ints(k, v);
+    fprintf(f, "fcfs-plan %llu", device_signature());
+    for (int i = 0; i < 16; ++i) fprintf(f, " %d", v[i]);
+    fprintf(f, " %d %d %d %d %d %d %d %d\n", t.WX, t.WY, t.WD, t.G, t.tma, t.threads, t.rs, t.psk);
+    fclose(f);
+}
+
 static PlanKey plan_key(const FwdParams& P, int ndim, int din, int dout) {
     PlanKey k;
     memset(&k, 0, sizeof k);
@@ -304,16 +390,36 @@ static PlanKey plan_key(const FwdParams& P, int ndim, int din, int dout) {
 }
 
 void set_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice t) {
+    std::call_once(g_cache_once, [] {
+        std::lock_guard<std::mutex> g(g_plan_mu);
+        load_plan_cache();
+    });
     std::lock_guard<std::mutex> g(g_plan_mu);
-    g_plans[plan_key(P, ndim, din, dout)] = t;
+    const PlanKey k = plan_key(P, ndim, din, dout);
+    g_plans[k] = t;
+    save_plan(k, t);
 }
 
 void clear_plans() {
+    std::call_once(g_cache_once, [] {});  // a cleared cache is not reloaded from the file
     std::lock_guard<std::mutex> g(g_plan_mu);
     g_plans.clear();
 }
 
+int plan_count() {
+    std::call_once(g_cache_once, [] {
+        std::lock_guard<std::mutex> g(g_plan_mu);
+        load_plan_cache();
+    });
+    std::lock_guard<std::mutex> g(g_plan_mu);
+    return (int)g_plans.size();
+}
+
 bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t) {
+    std::call_once(g_cache_once, [] {
+        std::lock_guard<std::mutex> g(g_plan_mu);
+        load_plan_cache();
+    });
     std::lock_guard<std::mutex> g(g_plan_mu);
     auto it = g_plans.find(plan_key(P, ndim, din, dout));
     if (it == g_plans.end()) return false;
@@ -446,6 +552,7 @@ int fcfs_geometry(int method, int r, int s, int K, long long n_in, long long* n_
 }
 
 int fcfs_forward(const fcfs_desc* d, const void* x, void* y, void* stream) {
+    NvtxRange nv("fcfs_forward");
     clear_error();
     int rc = validate_desc(d, true);
     if (rc) return rc;
@@ -1180,6 +1287,7 @@ size_t fcfs_backward_workspace(const fcfs_desc* d) {
 
 int fcfs_backward(const fcfs_desc* d, const void* x, const void* gy, void* gx, float* const* gw, void* workspace,
                   size_t ws_bytes, void* stream) {
+    NvtxRange nv("fcfs_backward");
     clear_error();
     int rc = validate_desc(d, true);
     if (rc) return rc;

@@ -3,9 +3,21 @@
 
 #include <stdarg.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fcfs_internal.cuh"
 
 namespace fcfs {
+
+// A named NVTX range for the duration of a scope: the C-ABI calls and the
+// serving loop's steps appear by name on profiler timelines (no cost without
+// an attached tool beyond a few instructions).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct TileChoice {
     int WX, WY, WD;  // windows per tile along x, y, depth
@@ -49,6 +61,7 @@ int launch_choice(const fcfs_desc* d, FwdParams& P, int ntk, const TileChoice& t
 TileChoice default_tiles(const FwdParams& P, bool is3d);
 void set_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice t);
 void clear_plans();
+int plan_count();
 bool get_plan(const FwdParams& P, int ndim, int din, int dout, TileChoice* t);
 int launch_planned(FwdParams& P, int ntk, bool is3d, int din, int dout, cudaStream_t st);
 int forward_planned(const fcfs_desc* d, const void* x, void* y, const Epi* epi, cudaStream_t st);

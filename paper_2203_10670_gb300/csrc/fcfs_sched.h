@@ -82,6 +82,7 @@ struct Request {
     double bytes = 0;         // algorithmic bytes (input + output)
     double admitted = 0;
     bool deferred_counted = false;
+    bool canceled = false;    // no further tiles; completes when its launched tiles finish
 };
 
 // One launch: the tile ranges it covers, per request slot.
@@ -187,10 +188,14 @@ class Scheduler {
             Request& r = it->second;
             r.done_tiles += p.count;
             if (r.done_tiles >= r.tiles) {
-                const double lat = now - r.arrival;
-                latencies_.push_back(lat);
-                out_pixels_ += r.out_pixels;
-                bytes_ += r.bytes;
+                if (r.canceled) {
+                    ++canceled_;
+                } else {
+                    latencies_.push_back(now - r.arrival);
+                    out_pixels_ += r.out_pixels;
+                    bytes_ += r.bytes;
+                    ++completed_;
+                }
                 if (release_pool && r.pool_off != SIZE_MAX) {
                     pool_.release(r.pool_off, r.out_bytes);
                     r.pool_off = SIZE_MAX;
@@ -198,13 +203,43 @@ class Scheduler {
                 free_slots_.push_back(r.slot);
                 done.push_back(r);
                 active_.erase(it);
-                ++completed_;
             }
         }
         return done;
     }
 
     // return the pool block of a completed request kept for the caller
+    // Cancel a request.  Queued: removed at once.  Admitted with none of its tiles in flight:
+    // finished at once (slot and pool memory returned).  Otherwise no further tile is launched and
+    // it finishes, uncounted in the latency and throughput totals, when its launched tiles
+    // complete.  Returns 1 when the request is finished now (*out holds it), 0 when it finishes
+    // later, -1 when the id is neither queued nor active.
+    int cancel(uint64_t id, bool release_pool, Request* out) {
+        for (auto it = queue_.begin(); it != queue_.end(); ++it)
+            if (it->id == id) {
+                *out = *it;
+                out->canceled = true;
+                queue_.erase(it);
+                ++canceled_;
+                return 1;
+            }
+        auto it = active_.find(id);
+        if (it == active_.end()) return -1;
+        Request& r = it->second;
+        r.canceled = true;
+        r.tiles = r.next_tile;  // nothing more is scheduled
+        if (r.done_tiles < r.tiles) return 0;
+        if (release_pool && r.pool_off != SIZE_MAX) {
+            pool_.release(r.pool_off, r.out_bytes);
+            r.pool_off = SIZE_MAX;
+        }
+        free_slots_.push_back(r.slot);
+        *out = r;
+        active_.erase(it);
+        ++canceled_;
+        return 1;
+    }
+
     void release_output(size_t off, size_t bytes) {
         if (off != SIZE_MAX) pool_.release(off, bytes);
     }
@@ -221,6 +256,7 @@ class Scheduler {
     size_t active() const { return active_.size(); }
     long long submitted() const { return submitted_; }
     long long completed() const { return completed_; }
+    long long canceled() const { return canceled_; }
     long long deferred() const { return deferred_; }
     int max_inflight_seen() const { return max_inflight_seen_; }
     const std::vector<double>& latencies() const { return latencies_; }
@@ -238,7 +274,7 @@ class Scheduler {
     std::map<uint64_t, Request> active_;
     std::vector<int> free_slots_;
     std::vector<double> latencies_;
-    long long submitted_ = 0, completed_ = 0, deferred_ = 0;
+    long long submitted_ = 0, completed_ = 0, deferred_ = 0, canceled_ = 0;
     int max_inflight_seen_ = 0;
     double out_pixels_ = 0, bytes_ = 0;
 };

@@ -6,11 +6,15 @@
 // the GPU overlaps on the device.  Each tile is computed exactly as the
 // standalone forward computes it, so a result does not depend on the mix.
 #include <chrono>
+#include <climits>
+#include <string>
 #include <condition_variable>
 #include <cstring>
 #include <mutex>
 #include <thread>
+#include <memory>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "fcfs_fwd_tile.cuh"
@@ -79,7 +83,7 @@ struct Server {
     StepRec steps[2];
     int step_next = 0;
     sched::Scheduler* S = nullptr;
-    std::map<uint64_t, ServeSlot> pending_params;  // submitted, waiting for a slot
+    std::unordered_map<uint64_t, std::unique_ptr<ServeSlot>> pending_params;  // submitted, waiting for a slot
     std::map<uint64_t, std::pair<void*, int>> out_of;  // id -> (y, dtype) for completed pooled outputs
     std::map<uint64_t, std::pair<size_t, size_t>> pooled;  // id -> (pool offset, bytes) kept for the caller
     std::deque<uint64_t> done_ids;
@@ -94,6 +98,7 @@ struct Server {
 };
 
 int launch_step(Server& sv, StepRec& R) {
+    NvtxRange nv("fcfs serve step");
     const long long n = R.step.tiles;
     if ((size_t)n > R.cap) return FCFS_ERR_NOMEM;
     long long k = 0;
@@ -130,30 +135,45 @@ void worker_loop(Server* sv) {
                 continue;
             }
             const double t = now_s();
+            // a canceled request's pool block is returned at once (its output is not read)
             auto done = sv->S->finish(R.step, t, sv->cfg.auto_release != 0);
             for (auto& r : done) {
                 sv->done_ids.push_back(r.id);
+                if (r.canceled) {
+                    if (r.pool_off != SIZE_MAX) sv->S->release_output(r.pool_off, r.out_bytes);
+                    sv->out_of.erase(r.id);
+                    continue;
+                }
                 if (r.pool_off != SIZE_MAX) sv->pooled[r.id] = {r.pool_off, r.out_bytes};
                 sv->last_done = t;
             }
             progressed = true;
         }
         if (progressed) sv->done_cv.notify_all();
-        // 2. admission: parameter slots are copied in stream order before any step uses them
+        // 2. admission: the parameter slots of this round are copied with one copy of the slot
+        //    range they span, in stream order before any step uses them (slots in between are
+        //    either active, copied unchanged, or free and not read by any launched step)
         auto adm = sv->S->admit(now_s());
+        int smin = INT_MAX, smax = -1;
         for (auto* r : adm) {
-            ServeSlot sl = sv->pending_params[r->id];
-            sv->pending_params.erase(r->id);
+            auto it = sv->pending_params.find(r->id);
+            ServeSlot& sl = sv->slots_host[r->slot];
+            sl = *it->second;
+            sv->pending_params.erase(it);
             if (r->pool_off != SIZE_MAX) {
                 sl.P.y = sv->pool_base + r->pool_off;
                 // with auto_release the block is reused once the request completes
                 if (!sv->cfg.auto_release) sv->out_of[r->id] = {sl.P.y, sv->cfg.out_dtype};
             }
-            sv->slots_host[r->slot] = sl;
-            cudaError_t e = cudaMemcpyAsync(sv->slots_dev + r->slot, sv->slots_host + r->slot, sizeof(ServeSlot),
-                                            cudaMemcpyHostToDevice, sv->stream);
-            if (e != cudaSuccess) sv->error = cuda_fail(e, "serve slot copy");
+            smin = std::min(smin, r->slot);
+            smax = std::max(smax, r->slot);
             progressed = true;
+        }
+        if (smax >= 0) {
+            cudaError_t e = cudaMemcpyAsync(sv->slots_dev + smin, sv->slots_host + smin,
+                                            sizeof(ServeSlot) * (size_t)(smax - smin + 1), cudaMemcpyHostToDevice,
+                                            sv->stream);
+            if (e != cudaSuccess) sv->error = cuda_fail(e, "serve slot copy");
         }
         // 3. launch the next step when a step record is free
         StepRec& R = sv->steps[sv->step_next];
@@ -262,56 +282,94 @@ int fcfs_serve_create(const fcfs_serve_config* cfg, void* stream, void** handle)
 
 int fcfs_serve_submit(void* h, const fcfs_desc* d, const void* x, void* y, double arrival_s,
                       unsigned long long* req_id) {
+    unsigned long long id = 0;
+    int n = 0;
+    const int rc = fcfs_serve_submit_batch(h, 1, d, &x, &y, &arrival_s, &id, &n);
+    if (req_id) *req_id = id;
+    return rc;
+}
+
+int fcfs_serve_submit_batch(void* h, int count, const fcfs_desc* descs, const void* const* xs, void* const* ys,
+                            const double* arrivals, unsigned long long* ids, int* n_submitted) {
     clear_error();
     Server* sv = (Server*)h;
+    if (n_submitted) *n_submitted = 0;
     if (!sv) return fail(FCFS_ERR_ARG, "null handle");
-    int rc = validate_desc(d, true);
-    if (rc) return rc;
-    if (d->ndim != 2) return fail(FCFS_ERR_UNSUPPORTED, "serving takes 2D images");
-    if (d->w2d) return fail(FCFS_ERR_UNSUPPORTED, "serving uses separable kernels");
-    for (int a = 0; a < 2; ++a)
-        if (d->axis[a].w) return fail(FCFS_ERR_UNSUPPORTED, "serving uses the fixed method tables");
-    if (!x) return fail(FCFS_ERR_ARG, "x is NULL");
-    // every slot of a step is stored by the grouped kernel instantiated for the
-    // server's out_dtype, caller-placed outputs included
-    if (d->dtype_out != sv->cfg.out_dtype)
-        return fail(FCFS_ERR_ARG, "dtype_out %d differs from the server's out_dtype %d", d->dtype_out,
-                    sv->cfg.out_dtype);
-    if (((uintptr_t)x) % dtype_size(d->dtype_in) || (y && ((uintptr_t)y) % dtype_size(d->dtype_out)))
-        return fail(FCFS_ERR_ARG, "x or y not aligned to its element size");
-    ServeSlot sl;
-    memset(&sl, 0, sizeof sl);
-    int ntk = 1;
-    rc = build_forward_params(d, x, y, &sl.P, &ntk);
-    if (rc) return rc;
-    if (ntk != 1 && ntk != 2 && ntk != 4) return fail(FCFS_ERR_UNSUPPORTED, "serving supports nearest, bilinear, bicubic");
-    plan_serve_tiles(sl.P);
-    sl.din = d->dtype_in;
-    sl.nt = ntk;
-    sched::Request r;
-    r.tiles = (long long)sl.P.tiles_x * sl.P.tiles_y * sl.P.planes;
-    if (r.tiles >= (1LL << 31)) return fail(FCFS_ERR_UNSUPPORTED, "request too large");
-    r.out_bytes = y ? 0 : (size_t)numel_out(d) * dtype_size(d->dtype_out);
-    r.out_pixels = (double)numel_out(d) / (double)d->c;
-    r.bytes = (double)numel_in(d) * dtype_size(d->dtype_in) + (double)numel_out(d) * dtype_size(d->dtype_out);
-    r.arrival = arrival_s;
+    if (count < 0 || (count > 0 && (!descs || !xs || !arrivals))) return fail(FCFS_ERR_ARG, "bad batch arguments");
+    // validate and plan every request outside the lock, then queue them in one critical section
+    std::vector<std::unique_ptr<ServeSlot>> slots;
+    std::vector<sched::Request> reqs;
+    slots.reserve(count);
+    reqs.reserve(count);
+    int status = FCFS_OK;
+    for (int k = 0; k < count; ++k) {
+        const fcfs_desc* d = descs + k;
+        const void* x = xs[k];
+        void* y = ys ? ys[k] : nullptr;
+        int rc = validate_desc(d, true);
+        if (!rc && d->ndim != 2) rc = fail(FCFS_ERR_UNSUPPORTED, "serving takes 2D images");
+        if (!rc && d->w2d) rc = fail(FCFS_ERR_UNSUPPORTED, "serving uses separable kernels");
+        for (int a = 0; !rc && a < 2; ++a)
+            if (d->axis[a].w) rc = fail(FCFS_ERR_UNSUPPORTED, "serving uses the fixed method tables");
+        if (!rc && !x) rc = fail(FCFS_ERR_ARG, "x is NULL");
+        // every slot of a step is stored by the grouped kernel instantiated for the
+        // server's out_dtype, caller-placed outputs included
+        if (!rc && d->dtype_out != sv->cfg.out_dtype)
+            rc = fail(FCFS_ERR_ARG, "dtype_out %d differs from the server's out_dtype %d", d->dtype_out,
+                      sv->cfg.out_dtype);
+        if (!rc && (((uintptr_t)x) % dtype_size(d->dtype_in) || (y && ((uintptr_t)y) % dtype_size(d->dtype_out))))
+            rc = fail(FCFS_ERR_ARG, "x or y not aligned to its element size");
+        auto sl = std::make_unique<ServeSlot>();
+        memset(sl.get(), 0, sizeof(ServeSlot));
+        int ntk = 1;
+        if (!rc) rc = build_forward_params(d, x, y, &sl->P, &ntk);
+        if (!rc && ntk != 1 && ntk != 2 && ntk != 4)
+            rc = fail(FCFS_ERR_UNSUPPORTED, "serving supports nearest, bilinear, bicubic (no antialiased windows)");
+        sched::Request r;
+        if (!rc) {
+            plan_serve_tiles(sl->P);
+            sl->din = d->dtype_in;
+            sl->nt = ntk;
+            r.tiles = (long long)sl->P.tiles_x * sl->P.tiles_y * sl->P.planes;
+            if (r.tiles >= (1LL << 31)) rc = fail(FCFS_ERR_UNSUPPORTED, "request too large");
+        }
+        if (rc) {
+            status = rc;
+            break;
+        }
+        r.out_bytes = y ? 0 : (size_t)numel_out(d) * dtype_size(d->dtype_out);
+        r.out_pixels = (double)numel_out(d) / (double)d->c;
+        r.bytes = (double)numel_in(d) * dtype_size(d->dtype_in) + (double)numel_out(d) * dtype_size(d->dtype_out);
+        r.arrival = arrivals[k];
+        reqs.push_back(r);
+        slots.push_back(std::move(sl));
+    }
+    const std::string why = status ? std::string(fcfs_last_error()) : std::string();
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->error) return fail(sv->error, "server stopped after an earlier error");
-    r.id = sv->next_id++;
-    if (r.tiles == 0) {  // empty output: complete at once
-        sv->done_ids.push_back(r.id);
-        if (req_id) *req_id = r.id;
-        return FCFS_OK;
+    int done = 0;
+    for (size_t k = 0; k < reqs.size(); ++k) {
+        sched::Request& r = reqs[k];
+        r.id = sv->next_id++;
+        if (r.tiles == 0) {  // empty output: complete at once
+            sv->done_ids.push_back(r.id);
+        } else {
+            if (!sv->S->submit(r)) {
+                ++sv->rejected;
+                sv->next_id--;
+                status = fail(FCFS_ERR_NOMEM, "output of %zu bytes exceeds the serving pool", r.out_bytes);
+                break;
+            }
+            sv->pending_params[r.id] = std::move(slots[k]);
+            if (sv->first_arrival < 0 || r.arrival < sv->first_arrival) sv->first_arrival = r.arrival;
+        }
+        if (ids) ids[k] = r.id;
+        ++done;
     }
-    if (!sv->S->submit(r)) {
-        ++sv->rejected;
-        return fail(FCFS_ERR_NOMEM, "output of %zu bytes exceeds the serving pool", r.out_bytes);
-    }
-    sv->pending_params[r.id] = sl;
-    if (sv->first_arrival < 0 || arrival_s < sv->first_arrival) sv->first_arrival = arrival_s;
-    if (req_id) *req_id = r.id;
-    sv->cv.notify_all();
-    return FCFS_OK;
+    if (n_submitted) *n_submitted = done;
+    if (done > 0) sv->cv.notify_all();
+    if (status && status != FCFS_ERR_NOMEM) return fail(status, "%s", why.c_str());
+    return status;
 }
 
 int fcfs_serve_poll(void* h, unsigned long long* done_ids, int max, int* n_done) {
@@ -353,6 +411,24 @@ int fcfs_serve_release(void* h, unsigned long long id) {
     return FCFS_OK;
 }
 
+int fcfs_serve_cancel(void* h, unsigned long long id) {
+    clear_error();
+    Server* sv = (Server*)h;
+    if (!sv) return fail(FCFS_ERR_ARG, "null handle");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sched::Request r;
+    const int rc = sv->S->cancel(id, true, &r);
+    if (rc < 0) return fail(FCFS_ERR_ARG, "request %llu is neither queued nor running", id);
+    sv->pending_params.erase(id);
+    sv->out_of.erase(id);
+    if (rc == 1) {
+        sv->done_ids.push_back(id);
+        sv->done_cv.notify_all();
+    }
+    sv->cv.notify_all();
+    return FCFS_OK;
+}
+
 int fcfs_serve_drain(void* h, int timeout_ms) {
     clear_error();
     Server* sv = (Server*)h;
@@ -376,6 +452,7 @@ int fcfs_serve_stats(void* h, fcfs_serve_stats_t* out) {
     const auto& L = sv->S->latencies();
     out->submitted = sv->S->submitted();
     out->completed = sv->S->completed();
+    out->canceled = sv->S->canceled();
     out->deferred = sv->S->deferred();
     out->rejected = sv->rejected;
     out->steps = sv->steps_launched;

@@ -10,6 +10,7 @@ using namespace fcfs;
 
 extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, void* stream, int reps, float* best_ms,
                                  int* n_candidates) {
+    NvtxRange nv("fcfs_tune_forward");
     clear_error();
     int rc = validate_desc(d, true);
     if (rc) return rc;
@@ -131,3 +132,5 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
 }
 
 extern "C" void fcfs_clear_plans(void) { clear_plans(); }
+
+extern "C" int fcfs_plan_count(void) { return plan_count(); }

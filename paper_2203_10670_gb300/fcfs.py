@@ -101,6 +101,11 @@ def fcfs_clear_plans() -> None:
     N.load().fcfs_clear_plans()
 
 
+def fcfs_plan_count() -> int:
+    """Plans in the process-wide cache (those tuned here, plus any loaded from FCFS_TUNE_CACHE)."""
+    return int(N.load().fcfs_plan_count())
+
+
 def fcfs_device_status(clear: bool = False) -> int:
     """Device status word (0 = every bounded wait completed); synchronizes."""
     v = N.load().fcfs_device_status(1 if clear else 0)
@@ -517,6 +522,23 @@ class Server:
                                           ctypes.byref(rid)), "fcfs_serve_submit")
         return rid.value
 
+    def submit_batch_raw(self, descs, x_ptrs, y_ptrs, arrivals) -> list:
+        """fcfs_serve_submit_batch with prebuilt descriptors (the caller keeps the inputs alive);
+        y_ptrs may be None (every output pooled).  Returns the ids; raises on the first invalid
+        request (the ones before it stay queued)."""
+        n = len(descs)
+        if n == 0:
+            return []
+        darr = (N.fcfs_desc * n)(*descs)
+        xarr = (ctypes.c_void_p * n)(*x_ptrs)
+        yarr = (ctypes.c_void_p * n)(*y_ptrs) if y_ptrs is not None else None
+        tarr = (ctypes.c_double * n)(*[float(t) for t in arrivals])
+        ids = (ctypes.c_ulonglong * n)()
+        done = ctypes.c_int()
+        check(self._lib.fcfs_serve_submit_batch(self._h, n, darr, xarr, yarr, tarr, ids, ctypes.byref(done)),
+              "fcfs_serve_submit_batch")
+        return list(ids)
+
     def poll(self, max_ids: int = 4096):
         ids = (ctypes.c_ulonglong * max_ids)()
         n = ctypes.c_int()
@@ -535,6 +557,10 @@ class Server:
 
     def release(self, rid: int) -> None:
         check(self._lib.fcfs_serve_release(self._h, rid), "fcfs_serve_release")
+
+    def cancel(self, rid: int) -> None:
+        """Give up on a request: queued ones leave at once, running ones stop receiving tiles."""
+        check(self._lib.fcfs_serve_cancel(self._h, rid), "fcfs_serve_cancel")
 
     def drain(self, timeout_ms: int = -1) -> None:
         check(self._lib.fcfs_serve_drain(self._h, timeout_ms), "fcfs_serve_drain")

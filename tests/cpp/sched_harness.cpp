@@ -153,6 +153,38 @@ static void randomized_invariants() {
     std::printf("ok randomized_invariants\n");
 }
 
+// Cancellation (a client that abandons its requests): queued ones leave at once,
+// admitted ones stop receiving tiles and finish when their launched tiles do,
+// uncounted in the latency and throughput totals; slots and pool memory return.
+static void cancel_requests() {
+    Scheduler S(1 << 20, 2, 8);
+    for (uint64_t id = 1; id <= 4; ++id) CHECK(S.submit(req(id, 10, 4096)));
+    CHECK(S.admit(0.0).size() == 2);  // 1 and 2 admitted, 3 and 4 queued
+    Request out;
+    CHECK(S.cancel(3, true, &out) == 1 && out.id == 3 && out.canceled);
+    CHECK(S.queued() == 1);
+    CHECK(S.cancel(99, true, &out) == -1);
+    // request 1 has tiles in flight: it stops receiving tiles and finishes with them
+    Step st = S.next_step();
+    CHECK(st.tiles == 8);
+    CHECK(S.cancel(1, true, &out) == 0);
+    auto done = S.finish(st, 1.0, true);
+    CHECK(done.size() == 1 && done[0].id == 1 && done[0].canceled);
+    CHECK(S.canceled() == 2 && S.completed() == 0 && S.latencies().empty());
+    // request 2 (4 tiles launched, 6 left) is not scheduled again after its cancel
+    CHECK(S.cancel(2, true, &out) == 1 && out.id == 2);
+    CHECK(S.admit(2.0).size() == 1);  // the freed slots admit request 4
+    Step s2 = S.next_step();
+    for (auto& p : s2.pieces) CHECK(p.id == 4);
+    while (!S.idle()) {
+        Step sn = s2.tiles ? s2 : S.next_step();
+        S.finish(sn, 3.0, true);
+        s2 = Step();
+    }
+    CHECK(S.completed() == 1 && S.canceled() == 3 && S.latencies().size() == 1);
+    std::printf("ok cancel_requests\n");
+}
+
 int main() {
     pool_basics();
     admission_by_footprint();
@@ -160,5 +192,6 @@ int main() {
     steps_round_robin_and_chunking();
     latency_and_percentiles();
     randomized_invariants();
+    cancel_requests();
     return 0;
 }

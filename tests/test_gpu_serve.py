@@ -162,5 +162,74 @@ def test_output_dtype_must_match_the_server(F):
             assert int(torch.count_nonzero(y.float())) == 0  # nothing was written
 
 
+def test_batch_submission(F):
+    # one call queues many requests; results equal the standalone forward; an invalid request
+    # stops the batch after the ones before it were queued
+    import ctypes
+
+    from paper_2203_10670_gb300 import _native as N
+
+    reqs = _requests(40, 6)
+    outs, descs, xs, ys = [], [], [], []
+    for x, ratio, m in reqs:
+        axes = [F.Axis(*ratio, m)] * 2
+        y = torch.empty(F.out_shape(x.shape, axes), device="cuda")
+        outs.append(y)
+        descs.append(F.make_desc(x.shape, axes, N.FCFS_U8, N.FCFS_F32))
+        xs.append(x.data_ptr())
+        ys.append(y.data_ptr())
+    with F.Server(1 << 30, max_inflight=16, tile_budget_per_step=64) as sv:
+        t = F.Server.clock()
+        ids = sv.submit_batch_raw(descs, xs, ys, [t] * len(descs))
+        assert len(set(ids)) == len(reqs)
+        sv.drain(60_000)
+        assert sorted(sv.poll()) == sorted(ids)
+        # an invalid third request: the first two are queued, its status is returned
+        bad = F.make_desc(reqs[0][0].shape, [F.Axis(3, 2, F.BILINEAR)] * 2, N.FCFS_U8, N.FCFS_BF16)
+        darr = (N.fcfs_desc * 4)(descs[0], descs[1], bad, descs[3])
+        xarr = (ctypes.c_void_p * 4)(*xs[:4])
+        yarr = (ctypes.c_void_p * 4)(*ys[:4])
+        tarr = (ctypes.c_double * 4)(t, t, t, t)
+        idarr = (ctypes.c_ulonglong * 4)()
+        n = ctypes.c_int()
+        rc = sv._lib.fcfs_serve_submit_batch(sv._h, 4, darr, xarr, yarr, tarr, idarr, ctypes.byref(n))
+        assert rc == N.FCFS_ERR_ARG and n.value == 2
+        sv.drain(60_000)
+        assert sorted(sv.poll()) == sorted(idarr[:2])
+    torch.cuda.synchronize()
+    for (x, ratio, m), y in zip(reqs, outs):
+        assert torch.equal(y, F.resize(x, [F.Axis(*ratio, m)] * 2))
+
+
+def test_cancel_queued_and_running_requests(F):
+    # a client that gives up on requests: queued ones leave at once, running ones stop receiving
+    # tiles; every id is still reported once, the rest of the stream completes normally
+    reqs = _requests(24, 7, lo=300, hi=600)
+    with F.Server(1 << 30, max_inflight=4, tile_budget_per_step=8, auto_release=False) as sv:
+        ids = [sv.submit(x, ratio, m) for x, ratio, m in reqs]
+        victims = set(ids[1::3])
+        for rid in sorted(victims):
+            sv.cancel(rid)
+        with pytest.raises(F.FCFSError):
+            sv.cancel(10 ** 9)  # unknown id
+        sv.drain(120_000)
+        done = []
+        while True:
+            got = sv.poll()
+            if not got:
+                break
+            done += got
+        assert sorted(done) == sorted(ids)
+        st = sv.stats()
+        assert st["canceled"] == len(victims) and st["completed"] == len(ids) - len(victims)
+        for rid, (x, ratio, m) in zip(ids, reqs):
+            if rid in victims:
+                with pytest.raises(F.FCFSError):
+                    sv.result(rid)  # no output for a canceled request
+            else:
+                assert torch.equal(sv.result(rid), F.resize(x, [F.Axis(*ratio, m)] * 2))
+                sv.release(rid)
+
+
 def test_device_status_clean_after_serving(F):
     assert F.fcfs_device_status(clear=True) == 0

@@ -16,5 +16,5 @@ def test_scheduler_core(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout + out.stderr
     for name in ("pool_basics", "admission_by_footprint", "slots_limit_inflight", "steps_round_robin_and_chunking",
-                 "latency_and_percentiles", "randomized_invariants"):
+                 "latency_and_percentiles", "randomized_invariants", "cancel_requests"):
         assert f"ok {name}" in out.stdout
