@@ -801,7 +801,7 @@ def full2d_only(args, device):
     print(json.dumps({"mode": "non-separable 5x5 learnable kernels, c3 tensor bf16 5/4", **r}), flush=True)
 
 
-def serve_bench(fcfs, inputs, device, count=None, passes=3, repeats=3):
+def serve_bench(fcfs, inputs, device, count=None, passes=3, repeats=3, inflight=256, budget=16384):
     """c4: continuous-batching server on 10,000 mixed requests (uint8, C=3, H and W
     log-uniform in [64, 2048], r/s and method uniform), inputs pre-staged on the
     device.  Closed-loop runs (the request list submitted `passes` times at once,
@@ -826,8 +826,8 @@ def serve_bench(fcfs, inputs, device, count=None, passes=3, repeats=3):
         xptrs = [base + int(o) for o in offs[:-1]]
 
         def run(rate, npass=1):
-            with fcfs.Server(max(8 << 30, 64 * max(out_bytes)), max_inflight=64, out_dtype=odt,
-                             tile_budget_per_step=8192, auto_release=True) as sv:
+            with fcfs.Server(max(8 << 30, 64 * max(out_bytes)), max_inflight=inflight, out_dtype=odt,
+                             tile_budget_per_step=budget, auto_release=True) as sv:
                 t0 = fcfs.Server.clock() + 0.01
                 if rate is None:  # closed loop: everything arrives at t0, queued in batches
                     for _ in range(npass):
@@ -956,7 +956,12 @@ def main():
             B.build()
             from paper_2203_10670_gb300 import fcfs, inputs
 
-            print(json.dumps({"mode": "c4 serving", **serve_bench(fcfs, inputs, device)}), flush=True)
+            res = {}
+            for inflight, budget in ((64, 8192), (256, 16384), (1024, 32768)):
+                r = serve_bench(fcfs, inputs, device, inflight=inflight, budget=budget)
+                res[f"inflight{inflight}_budget{budget}"] = {k: v for k, v in r.items()
+                                                             if "saturation" in k or "rate0.5" in k or "rate0.9" in k}
+            print(json.dumps({"mode": "c4 serving", **res}), flush=True)
             return
         run_ours(args, rank, world, device)
     finally:

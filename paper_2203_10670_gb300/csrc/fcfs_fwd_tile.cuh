@@ -24,8 +24,10 @@ __device__ __forceinline__ void stage_weights(float* dst, const AxisP& A, int c)
 
 // Input tile [rows][cols] of one depth plane, extended coordinates row0/col0,
 // with the padding rule as an index map.  One warp per row, lanes across
-// columns (coalesced).  src_plane == nullptr means the whole plane is the
-// constant pad value (constant padding in depth).
+// columns (coalesced); interior rows issue eight independent loads per lane
+// before storing them, so each warp keeps several loads in flight.
+// src_plane == nullptr means the whole plane is the constant pad value
+// (constant padding in depth).
 template <typename Tin>
 __device__ __forceinline__ void load_tile(float* sIn, int pitch, const Tin* src_plane, int H, int W, int row0,
                                           int col0, int rows, int cols, int pad, float padv) {
@@ -41,7 +43,15 @@ __device__ __forceinline__ void load_tile(float* sIn, int pitch, const Tin* src_
         const Tin* src = src_plane + (long long)sy * W;
         if (inside_x) {
             const Tin* s0 = src + col0;
-            for (int cx = lane; cx < cols; cx += 32) dst[cx] = load_f(s0 + cx);
+            constexpr int U = 8;
+            for (int cb = lane; cb < cols; cb += 32 * U) {
+                float v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = cb + 32 * u < cols ? load_f(s0 + cb + 32 * u) : 0.f;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (cb + 32 * u < cols) dst[cb + 32 * u] = v[u];
+            }
         } else {
             for (int cx = lane; cx < cols; cx += 32) {
                 const int sx = ext_index(col0 + cx, W, pad);

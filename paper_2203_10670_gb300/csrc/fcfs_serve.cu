@@ -25,7 +25,7 @@ namespace fcfs {
 namespace {
 
 constexpr int kServeThreads = 256;
-constexpr int kServeMaxSmem = 64 * 1024;
+constexpr int kServeMaxSmem = 48 * 1024;  // four CTAs per SM (the register limit too)
 
 // Device parameter slot of one admitted request.
 struct ServeSlot {
@@ -39,23 +39,235 @@ struct WorkItem {
     int tile;
 };
 
-template <typename Tin, typename Tout>
-__device__ __forceinline__ void serve_tile(const FwdParams& P, int nt, long long tile, float* smem) {
-    if (nt == 1) fwd2d_tile<1, Tin, Tout>(P, tile, smem);
-    else if (nt == 2) fwd2d_tile<2, Tin, Tout>(P, tile, smem);
-    else fwd2d_tile<4, Tin, Tout>(P, tile, smem);
+// Per-request scalars of the tile computation, staged in shared memory when a
+// CTA moves to another request, and the per-tile geometry computed once by one
+// thread.  Every thread then reads them from shared memory into registers:
+// the slot itself lives in global memory, and reading its fields throughout
+// the passes would reload them at global latency.
+struct ServeReq {
+    const void* x;
+    void* y;
+    int din, nt;
+    int H, W, Ho, Wo;
+    int rx, sx, ry, sy, lox, loy, spanx, spany;
+    int nwinx, nwiny, tiles_x, tiles_y, WX, WY, OX, G, ICp, IR;
+    int pad;
+    float padv;
+};
+
+struct ServeTile {
+    int plane, ix0, iy0, nwx, nwy, cols, rows, col0, row0;
+};
+
+// Four adjacent outputs of one row: a 16-byte (FP32) or 8-byte (BF16) store
+// when aligned and inside the row, else element by element.
+__device__ __forceinline__ void store4(float* p, int nvalid, bool vec, const float* a) {
+    if (vec) {
+        *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+        return;
+    }
+    for (int i = 0; i < nvalid; ++i) p[i] = a[i];
+}
+__device__ __forceinline__ void store4(__nv_bfloat16* p, int nvalid, bool vec, const float* a) {
+    if (vec) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(a[0], a[1]), hi = __floats2bfloat162_rn(a[2], a[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&lo);
+        u.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(p) = u;
+        return;
+    }
+    for (int i = 0; i < nvalid; ++i) p[i] = __float2bfloat16_rn(a[i]);
 }
 
-// K6: one CTA per work item; the item names the request slot and its tile.
+// One tile: stage the padded input (index map), x pass with one window per
+// thread (its span samples loaded once for every phase), y pass with four
+// adjacent output columns per thread (vector shared-memory loads and stores).
+template <int NT, typename Tin, typename Tout>
+__device__ __forceinline__ void serve_tile_body(const ServeReq& q, const ServeTile& g, const float* sWx,
+                                                const float* sWy, const short* offx, const short* offy, float* sIn) {
+    constexpr int MAXSPAN = 24;  // span of a window: phases' taps (fixed methods, r <= 16 here)
+    const int OX = q.OX;
+    // the intermediate starts on a 16-byte boundary (vector reads in the y pass)
+    float* sH = sIn + ((q.IR * q.ICp + 3) & ~3);
+    const Tin* xp = static_cast<const Tin*>(q.x) + (long long)g.plane * q.H * q.W;
+    load_tile<Tin>(sIn, q.ICp, xp, q.H, q.W, g.row0, g.col0, g.rows, g.cols, q.pad, q.padv);
+    __syncthreads();
+    // ---- x pass: thread = (window ixl, row group); sH[ry][ixl rx + jx]
+    const int rx = q.rx;
+    if (rx <= 8 && q.spanx <= MAXSPAN) {
+        const int nthr = g.nwx;
+        const int G1 = blockDim.x / nthr;
+        const int ixl = threadIdx.x % nthr, grp = threadIdx.x / nthr;
+        if (grp < G1) {
+            for (int ry = grp; ry < g.rows; ry += G1) {
+                const float* row = sIn + ry * q.ICp + ixl * q.sx;
+                float* dst = sH + ry * OX + ixl * rx;
+                for (int jx = 0; jx < rx; ++jx) {
+                    const float* src = row + offx[jx];
+                    const float* w = sWx + jx * 4;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) acc = fmaf(w[t], src[t], acc);
+                    dst[jx] = acc;
+                }
+            }
+        }
+    } else {
+        const int ox = threadIdx.x % OX, grp = threadIdx.x / OX, G = q.G;
+        const int jx = ox % rx, ixl = ox / rx;
+        if (ixl < g.nwx && grp < G) {
+            float w[NT];
+#pragma unroll
+            for (int t = 0; t < NT; ++t) w[t] = sWx[jx * 4 + t];
+            const float* base = sIn + ixl * q.sx + offx[jx];
+            for (int ry = grp; ry < g.rows; ry += G) {
+                const float* row = base + ry * q.ICp;
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) acc = fmaf(w[t], row[t], acc);
+                sH[ry * OX + ox] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- y pass: thread = (four output columns, row group); outputs at pixel-shuffled positions
+    const int ncolv = g.nwx * rx;          // valid tile columns
+    const int nq = (OX + 3) / 4;           // column quads of the tile
+    const int G2 = blockDim.x / nq;
+    const int cq = threadIdx.x % nq, grp = threadIdx.x / nq;
+    const int ox = cq * 4;
+    const int gox = g.ix0 * rx + ox;
+    if (grp >= G2 || ox >= ncolv || gox >= q.Wo) return;
+    const int nvalid = min(4, min(ncolv - ox, q.Wo - gox));
+    Tout* yp = static_cast<Tout*>(q.y) + (long long)g.plane * q.Ho * q.Wo + gox;
+    const bool vec = nvalid == 4 && (OX % 4) == 0 &&
+                     (reinterpret_cast<uintptr_t>(yp) % (4 * sizeof(Tout))) == 0 && (q.Wo % 4) == 0;
+    const int nrow = g.nwy * q.ry;
+    for (int orow = grp; orow < nrow; orow += G2) {
+        const int iyl = orow / q.ry, jy = orow - iyl * q.ry;
+        const int oy = (g.iy0 + iyl) * q.ry + jy;
+        if (oy >= q.Ho) continue;
+        const float* col = sH + (iyl * q.sy + offy[jy]) * OX + ox;
+        const float* wy = sWy + jy * 4;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            float h[4];
+            if ((OX % 4) == 0) {
+                const float4 v = *reinterpret_cast<const float4*>(col + t * OX);
+                h[0] = v.x, h[1] = v.y, h[2] = v.z, h[3] = v.w;
+            } else {
+                for (int i = 0; i < 4; ++i) h[i] = ox + i < OX ? col[t * OX + i] : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fmaf(wy[t], h[i], acc[i]);
+        }
+        store4(yp + (long long)oy * q.Wo, nvalid, vec, acc);
+    }
+}
+
+template <typename Tin, typename Tout>
+__device__ __forceinline__ void serve_tile(const ServeReq& q, const ServeTile& g, const float* sWx, const float* sWy,
+                                           const short* offx, const short* offy, float* sIn) {
+    if (q.nt == 1) serve_tile_body<1, Tin, Tout>(q, g, sWx, sWy, offx, offy, sIn);
+    else if (q.nt == 2) serve_tile_body<2, Tin, Tout>(q, g, sWx, sWy, offx, offy, sIn);
+    else serve_tile_body<4, Tin, Tout>(q, g, sWx, sWy, offx, offy, sIn);
+}
+
+// K6: a persistent grouped kernel.  CTA b takes the work items [b per, (b+1) per)
+// in order (the items of one request are consecutive, so the request's
+// parameters are staged once per run of its tiles); each item names a request
+// slot and one of its tiles.
 template <typename Tout>
 __global__ void __launch_bounds__(kServeThreads) fcfs_serve_grouped(const ServeSlot* __restrict__ slots,
-                                                                     const WorkItem* __restrict__ work) {
-    extern __shared__ float smem[];
-    const WorkItem w = work[blockIdx.x];
-    const ServeSlot& S = slots[w.slot];
-    if (S.din == FCFS_U8) serve_tile<uint8_t, Tout>(S.P, S.nt, w.tile, smem);
-    else if (S.din == FCFS_F32) serve_tile<float, Tout>(S.P, S.nt, w.tile, smem);
-    else serve_tile<__nv_bfloat16, Tout>(S.P, S.nt, w.tile, smem);
+                                                                     const WorkItem* __restrict__ work, int n_items) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ ServeReq sq;
+    __shared__ ServeTile st;
+    __shared__ float sWx[kMaxR * 4], sWy[kMaxR * 4];
+    __shared__ short offx[kMaxR], offy[kMaxR];
+    const int per = (n_items + gridDim.x - 1) / gridDim.x;
+    const int k0 = blockIdx.x * per, k1 = min(n_items, k0 + per);
+    int last_slot = -1;
+    for (int k = k0; k < k1; ++k) {
+        const WorkItem w = work[k];
+        __syncthreads();  // the previous tile is done with the staged parameters and buffers
+        if (w.slot != last_slot) {
+            const ServeSlot& S = slots[w.slot];
+            const AxisP& AX = S.P.ax[2];
+            const AxisP& AY = S.P.ax[1];
+            for (int e = threadIdx.x; e < AX.r * 4; e += blockDim.x) {
+                const int j = e >> 2, t = e & 3;
+                sWx[e] = t < AX.nt_src ? AX.wf[j * AX.nt_src + t] : 0.f;
+            }
+            for (int e = threadIdx.x; e < AY.r * 4; e += blockDim.x) {
+                const int j = e >> 2, t = e & 3;
+                sWy[e] = t < AY.nt_src ? AY.wf[j * AY.nt_src + t] : 0.f;
+            }
+            for (int e = threadIdx.x; e < AX.r; e += blockDim.x) offx[e] = AX.off[e];
+            for (int e = threadIdx.x; e < AY.r; e += blockDim.x) offy[e] = AY.off[e];
+            if (threadIdx.x == 0) {
+                ServeReq q;
+                q.x = S.P.x;
+                q.y = S.P.y;
+                q.din = S.din;
+                q.nt = S.nt;
+                q.H = AY.n_in;
+                q.W = AX.n_in;
+                q.Ho = AY.n_out;
+                q.Wo = AX.n_out;
+                q.rx = AX.r;
+                q.sx = AX.s;
+                q.ry = AY.r;
+                q.sy = AY.s;
+                q.lox = AX.lo;
+                q.loy = AY.lo;
+                q.spanx = AX.span;
+                q.spany = AY.span;
+                q.nwinx = AX.n_win;
+                q.nwiny = AY.n_win;
+                q.tiles_x = S.P.tiles_x;
+                q.tiles_y = S.P.tiles_y;
+                q.WX = S.P.WX;
+                q.WY = S.P.WY;
+                q.OX = S.P.OX;
+                q.G = S.P.G;
+                q.ICp = S.P.ICp;
+                q.IR = S.P.IR;
+                q.pad = S.P.pad;
+                q.padv = S.P.padv;
+                sq = q;
+            }
+            last_slot = w.slot;
+        }
+        if (threadIdx.x == 0) {
+            // tile index -> geometry in 32-bit arithmetic (a request has fewer than 2^31 tiles)
+            const ServeSlot& S = slots[w.slot];
+            const int txy = S.P.tiles_x * S.P.tiles_y;
+            ServeTile g;
+            g.plane = w.tile / txy;
+            const int rem = w.tile - g.plane * txy;
+            const int ty = rem / S.P.tiles_x, tx = rem - ty * S.P.tiles_x;
+            const AxisP& AX = S.P.ax[2];
+            const AxisP& AY = S.P.ax[1];
+            g.ix0 = tx * S.P.WX;
+            g.iy0 = ty * S.P.WY;
+            g.nwx = min(S.P.WX, AX.n_win - g.ix0);
+            g.nwy = min(S.P.WY, AY.n_win - g.iy0);
+            g.cols = (g.nwx - 1) * AX.s + AX.span;
+            g.rows = (g.nwy - 1) * AY.s + AY.span;
+            g.col0 = g.ix0 * AX.s + AX.lo;
+            g.row0 = g.iy0 * AY.s + AY.lo;
+            st = g;
+        }
+        __syncthreads();
+        const ServeReq q = sq;
+        const ServeTile g = st;
+        if (q.din == FCFS_U8) serve_tile<uint8_t, Tout>(q, g, sWx, sWy, offx, offy, smem);
+        else if (q.din == FCFS_F32) serve_tile<float, Tout>(q, g, sWx, sWy, offx, offy, smem);
+        else serve_tile<__nv_bfloat16, Tout>(q, g, sWx, sWy, offx, offy, smem);
+    }
 }
 
 double now_s() {
@@ -80,7 +292,8 @@ struct Server {
     unsigned char* pool_base = nullptr;
     ServeSlot* slots_dev = nullptr;
     ServeSlot* slots_host = nullptr;  // pinned, one per slot
-    StepRec steps[2];
+    static constexpr int kSteps = 4;  // grouped launches that may be queued on the stream at once
+    StepRec steps[kSteps];
     int step_next = 0;
     sched::Scheduler* S = nullptr;
     std::unordered_map<uint64_t, std::unique_ptr<ServeSlot>> pending_params;  // submitted, waiting for a slot
@@ -95,6 +308,7 @@ struct Server {
     uint64_t next_id = 1;
     long long steps_launched = 0, rejected = 0;
     double first_arrival = -1, last_done = -1;
+    int grid_cap = 1;  // resident CTAs of the grouped kernel (persistent grid)
 };
 
 int launch_step(Server& sv, StepRec& R) {
@@ -106,10 +320,11 @@ int launch_step(Server& sv, StepRec& R) {
         for (long long t = 0; t < p.count; ++t) R.host[k++] = WorkItem{p.slot, (int)(p.first + t)};
     cudaError_t e = cudaMemcpyAsync(R.dev, R.host, n * sizeof(WorkItem), cudaMemcpyHostToDevice, sv.stream);
     if (e != cudaSuccess) return cuda_fail(e, "serve work list copy");
+    const unsigned grid = (unsigned)std::min<long long>(n, (long long)sv.grid_cap);
     if (sv.cfg.out_dtype == FCFS_BF16)
-        fcfs_serve_grouped<__nv_bfloat16><<<(unsigned)n, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev);
+        fcfs_serve_grouped<__nv_bfloat16><<<grid, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev, (int)n);
     else
-        fcfs_serve_grouped<float><<<(unsigned)n, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev);
+        fcfs_serve_grouped<float><<<grid, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev, (int)n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "serve grouped launch");
     e = cudaEventRecord(R.ev, sv.stream);
@@ -182,27 +397,37 @@ void worker_loop(Server* sv) {
             if (R.step.tiles > 0) {
                 const int rc = launch_step(*sv, R);
                 if (rc != FCFS_OK) sv->error = rc;
-                sv->step_next ^= 1;
+                sv->step_next = (sv->step_next + 1) % Server::kSteps;
                 progressed = true;
             }
         }
         if (!progressed) {
-            const bool busy = sv->steps[0].busy || sv->steps[1].busy;
-            // GPU busy: poll again soon; idle: sleep until a submission arrives
-            sv->cv.wait_for(lk, busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(5));
+            bool busy = false;
+            for (auto& R : sv->steps) busy |= R.busy;
+            if (busy) {
+                // GPU busy: poll again after yielding the processor (a timed sleep would often
+                // oversleep the step and leave the GPU idle)
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            } else {
+                // idle: sleep until a submission arrives
+                sv->cv.wait_for(lk, std::chrono::milliseconds(5));
+            }
         }
     }
 }
 
-// Tile plan for serving: 256-thread CTAs, about 128 output columns, shared
-// memory within the grouped kernel's budget.
+// Tile plan for serving: 256-thread CTAs, about 128 output columns and 64
+// output rows, shared memory within the grouped kernel's budget.
 void plan_serve_tiles(FwdParams& P) {
-    int WX = std::max(1, 128 / P.ax[2].r), WY = std::max(1, 32 / P.ax[1].r);
+    int WX = std::max(1, 128 / P.ax[2].r), WY = std::max(1, 64 / P.ax[1].r);
     for (int it = 0; it < 64; ++it) {
         apply_tiles(P, false, WX, WY, 1, 0);
         const int G = std::max(1, kServeThreads / P.OX);
         P.G = G;
-        if (P.OX <= kServeThreads && forward_smem_bytes(P, false) <= (size_t)kServeMaxSmem) return;
+        const size_t need = (((size_t)P.IR * P.ICp + 3) / 4 * 4 + (size_t)P.IR * P.OX) * sizeof(float);
+        if (P.OX <= kServeThreads && need <= (size_t)kServeMaxSmem) return;
         if (P.OX > kServeThreads && WX > 1) WX = (WX + 1) / 2;
         else if (WY > 1) WY = (WY + 1) / 2;
         else if (WX > 1) WX = (WX + 1) / 2;
@@ -272,6 +497,17 @@ int fcfs_serve_create(const fcfs_serve_config* cfg, void* stream, void** handle)
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(fcfs_serve_grouped<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kServeMaxSmem);
+    }
+    if (e == cudaSuccess) {
+        int sms = 0, per_sm = 0, dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, cfg->out_dtype == FCFS_BF16 ? (const void*)fcfs_serve_grouped<__nv_bfloat16>
+                                                     : (const void*)fcfs_serve_grouped<float>,
+                kServeThreads, kServeMaxSmem);
+        sv->grid_cap = std::max(1, sms * per_sm);
     }
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "serve buffers"));
     sv->S = new sched::Scheduler(cfg->hbm_budget_bytes, cfg->max_inflight, cfg->tile_budget_per_step);
