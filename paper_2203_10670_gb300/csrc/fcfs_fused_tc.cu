@@ -4,9 +4,14 @@
 // pixels) product per tile: tcgen05.mma (kind::tf32, M = 128 output channels,
 // N = 256 pixels, K = 8 input channels per instruction) accumulates it in
 // tensor memory while the CUDA cores produce the next eight FCFS planes.
-// FP32 accuracy from TF32 units: every operand is split into a TF32 head and
-// the (exactly representable) remainder, and D += Ah Bh + Ah Bl + Al Bh
-// (the dropped Al Bl term is below 2^-21 of each product).
+// FP32 accuracy from TF32 units: every operand x is split into its TF32 head
+// h (x with the 13 low mantissa bits cleared) and the remainder l = x - h,
+// which FP32 holds exactly; |l| < 2^-10 |x| and l has up to 13 significant
+// bits, of which the tensor cores read the top 11 (TF32), so they see l to
+// within 2^-10 |l| < 2^-20 |x|.  D += Ah Bh + Ah Bl + Al Bh: the two
+// remainder terms are each within 2^-20 |A B| of their exact values and the
+// dropped Al Bl term is below 2^-20 |A B|, so every product is accurate to
+// about 3 x 2^-20 of its magnitude, inside the FP32 bar of the layer.
 //
 // Per CTA: one output tile (at most 256 pixels) of one image, 128 output
 // channels.  Shared memory holds both splits of the CTA's mix rows (operand
