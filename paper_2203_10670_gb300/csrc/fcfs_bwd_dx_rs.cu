@@ -29,22 +29,35 @@ __device__ __forceinline__ void stage_adj_span(float* WF, const AxisP& A, const 
     }
 }
 
-// XSPEC: one adjoint window per thread in the x pass (lanes stride r samples).
-// VW = 1: scalar loads (bank-conflict free for odd r or r * sizeof(Tg) <= 4).
-// VW = r (r * sizeof(Tg) = 8 or 16 bytes): a window's samples are read as
+// x pass: one adjoint window per thread (lanes stride r samples).  VW = 1:
+// scalar loads (bank-conflict free for odd r or r * sizeof(Tg) <= 4).  VW = r
+// (r * sizeof(Tg) = 8 or 16 bytes): a window's samples are read as
 // VW-aligned vectors, so the lanes' loads are contiguous; the planner takes
 // this path only when every window starts on a VW boundary of the staged row
-// (the adjoint's first g offset a multiple of r), and the x weight rows are
-// the span rounded up to VW.
-// Otherwise one intermediate column per thread.  Four CTAs per SM (at most 64
-// registers a thread): the passes are latency-bound between barriers, and the
-// extra resident CTAs measured faster than the larger register budget.
-template <int S, int SPAN, int VW, typename Tg, typename Tx, bool XSPEC>
-__global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
-    constexpr int SPANX = (SPAN + VW - 1) / VW * VW;
+// (the adjoint's first g offset a multiple of r).  The window's samples are
+// summed in tap pairs with packed FP32 FMAs (even and odd taps in the two
+// lanes of a pair, added at the end), so the x weight rows are the span
+// rounded up to an even count (and to VW).
+//
+// y pass: YV = 4 adjacent real columns per thread.  Their intermediate
+// values are read as one vector per row and each sum runs in the lanes of
+// packed FMAs against duplicated weight pairs, in tap order; the YV outputs
+// of a row are one vector store.  The intermediate rows are laid out so the
+// tile's first real column starts on a 16-byte boundary.  YV = 1: one column
+// per thread with scalar FMAs (rows whose length is not a multiple of four).
+//
+// Two CTAs per SM (the staged tiles take about 110 KB of shared memory), so
+// up to 128 registers a thread.
+template <int S, int SPAN, int VW, typename Tg, int YV>
+__global__ void __launch_bounds__(256, 2) fcfs_bwd_dx2d_rs(const __grid_constant__ TmaDxParams T) {
+    constexpr int VP = VW > 2 ? VW : 2;
+    constexpr int SPANX = (SPAN + VP - 1) / VP * VP;
+    constexpr int NP = SPANX / 2;  // tap pairs of the x pass
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
-    __shared__ float sWFx[S * SPANX], sWFy[S * SPAN];
+    __shared__ __align__(16) float sWFx[S * SPANX];
+    __shared__ float sWFy[S * SPAN];
+    __shared__ __align__(16) float2 sWY2[S * SPAN];  // the y weights, each duplicated into a pair
     const AdjP& JX = T.aj[2];
     const AdjP& JY = T.aj[1];
     float* sF = reinterpret_cast<float*>(smem_raw + T.fx_off);
@@ -52,46 +65,51 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
     const int NS = T.stages;
     const int QX = T.QX, GBW = T.GBW, FXP = T.FXP, R = JX.r;
     const int Nx = JX.n_x, Ny = JY.n_x;
-    // x pass mapping
-    const int XT = XSPEC ? T.WAcap : T.WAcap * S;
+    // x pass mapping: a row of windows per group of WAcap threads
+    const int XT = T.WAcap;
     const int G1 = blockDim.x / XT;
     const int xi = threadIdx.x % XT, g1 = threadIdx.x / XT;
-    // y pass mapping
-    const int G2 = blockDim.x / QX;
-    const int cl = threadIdx.x % QX, g2 = threadIdx.x / QX;
+    // y pass mapping: YV columns per thread, groups over the adjoint windows
+    const int NCY = QX / YV;
+    const int G2 = blockDim.x / NCY;
+    const int cy = threadIdx.x % NCY, g2 = threadIdx.x / NCY;
+    // second stage of edge tiles (fold in y): one column per thread
+    const int G3 = blockDim.x / QX;
+    const int cl = threadIdx.x % QX, g3 = threadIdx.x / QX;
 
-    const int ntiles = (int)T.ntiles;
-    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-    int tile = blockIdx.x * per;
-    const int tile_end = min(ntiles, tile + per);
-    if (tile >= tile_end) return;
+    const TileDeal deal = deal_tiles((int)T.ntiles, T.chunk);
+    const int ntile = deal.n;
+    auto tile_of = [&](int k) { return deal.tile(k); };
+    if (ntile <= 0) return;
     // geometry of the tile in each stage, computed once by the thread that issues its copy
     __shared__ DxGeo sgeo[4];
-    __shared__ DxWalk walk;  // the next tile to issue
     if (threadIdx.x == 0) {
         for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
         s_abort = 0;
-        dx_walk_init(T, walk, tile);
-        for (int k = 0; k < NS && tile + k < tile_end; ++k) {
-            sgeo[k] = dx_walk_geo(T, walk);
+        for (int k = 0; k < NS && k < ntile; ++k) {
+            sgeo[k] = dx_geo(T, tile_of(k));
             issue<Tg>(T, sgeo[k], smem_raw + k * T.buf_bytes, &bars[k]);
-            dx_walk_next(T, walk);
         }
     }
     __syncthreads();
     const bool learn = T.ax[2].learn || T.ax[1].learn;
     int cur_c = -1;
+    // the weights stay in registers across tiles (reloaded when the channel changes)
+    float2 wf[S][NP];       // x: tap pairs
+    // y: each tap duplicated into a pair; wide weight sets are read from shared memory per use
+    constexpr bool HOLD_Y = YV > 1 && S * SPAN <= 24;
+    float2 wy[HOLD_Y ? S : 1][HOLD_Y ? SPAN : 1];
     int stg = 0;
     uint32_t phase = 0;
-    for (; tile < tile_end; ++tile) {
+    for (int k = 0; k < ntile; ++k) {
         unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
         const Tg* G0 = reinterpret_cast<const Tg*>(bufk);
         // one warp waits for the copy; the barrier releases the others
         if (threadIdx.x < 32 && !mbar_wait(&bars[stg], phase, &g_status_bwd_tma)) s_abort = 1;
         __syncthreads();
         if (s_abort) {
-            if (threadIdx.x == 0) drain_ring(bars, NS, stg, phase, min(NS, tile_end - tile), &g_status_bwd_tma);
+            if (threadIdx.x == 0) drain_ring(bars, NS, stg, phase, min(NS, ntile - k), &g_status_bwd_tma);
             return;
         }
         const DxGeo geo = sgeo[stg];
@@ -99,8 +117,20 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
             // the previous tile ended with a barrier: no thread still reads the weights
             stage_adj_span<S, SPANX>(sWFx, T.ax[2], JX, geo.c, 0);
             stage_adj_span<S, SPAN>(sWFy, T.ax[1], JY, geo.c, 0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < S * SPAN; e += blockDim.x) sWY2[e] = make_float2(sWFy[e], sWFy[e]);
             cur_c = geo.c;
             __syncthreads();
+#pragma unroll
+            for (int u = 0; u < S; ++u)
+#pragma unroll
+                for (int p = 0; p < NP; ++p) wf[u][p] = *reinterpret_cast<const float2*>(sWFx + u * SPANX + 2 * p);
+            if constexpr (HOLD_Y) {
+#pragma unroll
+                for (int u = 0; u < S; ++u)
+#pragma unroll
+                    for (int qq = 0; qq < SPAN; ++qq) wy[u][qq] = sWY2[u * SPAN + qq];
+            }
         }
         // windows start on VW boundaries (planner); a violation is reported, not read past
         if (VW > 1 && (geo.xoff & (VW - 1)) != 0) {
@@ -110,58 +140,60 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
         const int nAX = geo.X.ahi >= geo.X.alo ? geo.X.ahi - geo.X.alo + 1 : 0;
         const int nAY = geo.Y.ahi >= geo.Y.alo ? geo.Y.ahi - geo.Y.alo + 1 : 0;
         const int nGR = nAY ? (nAY - 1) * R + SPAN : 0;
-        const int fxb = geo.X.alo * S + JX.lo_out;  // extended index of intermediate column 0
-        // ---- pass x (adjoint along x) for every staged g row
-        if (g1 < G1) {
-            if (XSPEC) {
-                if (xi < nAX) {
-                    float wf[S][SPANX];
+        // intermediate column of extended index v: v - fxb, with fxb = fxw - sh, where fxw is the
+        // extended index of the first adjoint window's first output and sh puts the tile's first
+        // real column on a multiple of four
+        const int fxw = geo.X.alo * S + JX.lo_out;
+        const int sh = (fxw - geo.qx0) & 3;
+        const int fxb = fxw - sh;
+        // ---- pass x (adjoint along x) for every staged g row, tap pairs in packed FMAs
+        if (g1 < G1 && xi < nAX) {
+            const Tg* src = G0 + g1 * GBW + (geo.xoff & ~(VW - 1)) + xi * R;
+            float* dst = sF + g1 * FXP + sh + xi * S;
+            // two rows per step (independent chains in flight); the second is skipped past the end
+            for (int gr = g1; gr < nGR; gr += 2 * G1) {
+                const bool two = gr + G1 < nGR;
+                float v[2][SPANX];
 #pragma unroll
-                    for (int u = 0; u < S; ++u)
+                for (int k = 0; k < 2; ++k) {
+                    const Tg* sk = src + (two ? k : 0) * G1 * GBW;
+                    if constexpr (VW > 1) {
 #pragma unroll
-                        for (int q = 0; q < SPANX; ++q) wf[u][q] = sWFx[u * SPANX + q];
-                    const Tg* src = G0 + g1 * GBW + (geo.xoff & ~(VW - 1)) + xi * R;
-                    float* dst = sF + g1 * FXP + xi * S;
-                    for (int gr = g1; gr < nGR; gr += G1) {
-                        float v[SPANX];
-                        if constexpr (VW > 1) {
+                        for (int q = 0; q < SPANX; q += VW) load_vec<VW, Tg>(sk + q, v[k] + q);
+                    } else {
 #pragma unroll
-                            for (int q = 0; q < SPANX; q += VW) load_vec<VW, Tg>(src + q, v + q);
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < SPANX; ++q) v[q] = to_f<Tg>(src[q]);
-                        }
-#pragma unroll
-                        for (int u = 0; u < S; ++u) {
-                            float acc = 0.f;
-#pragma unroll
-                            for (int q = 0; q < SPANX; ++q) acc = fmaf(wf[u][q], v[q], acc);
-                            dst[u] = acc;
-                        }
-                        src += G1 * GBW;
-                        dst += G1 * FXP;
+                        for (int q = 0; q < SPANX; ++q) v[k][q] = to_f<Tg>(sk[q]);
                     }
                 }
-            } else {
-                const int aw = xi / S, u = xi - aw * S;
-                if (aw < nAX) {
-                    float wf[SPAN];
 #pragma unroll
-                    for (int q = 0; q < SPAN; ++q) wf[q] = sWFx[u * SPAN + q];
-                    const Tg* src = G0 + g1 * GBW + geo.xoff + aw * R;
-                    float* dst = sF + g1 * FXP + xi;
-                    for (int gr = g1; gr < nGR; gr += G1) {
-                        float acc = 0.f;
+                for (int k = 0; k < 2; ++k) {
+                    float o[S];
 #pragma unroll
-                        for (int q = 0; q < SPAN; ++q) acc = fmaf(wf[q], to_f<Tg>(src[q]), acc);
-                        *dst = acc;
-                        src += G1 * GBW;
-                        dst += G1 * FXP;
+                    for (int u = 0; u < S; ++u) {
+                        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int p = 0; p < NP; ++p)
+                            acc = __ffma2_rn(wf[u][p], make_float2(v[k][2 * p], v[k][2 * p + 1]), acc);
+                        o[u] = acc.x + acc.y;
+                    }
+                    if (k == 0 || two) {
+#pragma unroll
+                        for (int u = 0; u < S; ++u) dst[k * G1 * FXP + u] = o[u];
                     }
                 }
+                src += 2 * G1 * GBW;
+                dst += 2 * G1 * FXP;
             }
         }
         __syncthreads();
+        // the g tile is consumed: a tile whose y pass does not stage its outputs in this buffer
+        // lets the copy NS tiles ahead start now
+        const bool ypath_smem = geo.Y.left || geo.Y.right || !geo.Y.covered;
+        const bool early = !ypath_smem;
+        if (early && threadIdx.x == 0 && k + NS < ntile) {
+            sgeo[stg] = dx_geo(T, tile_of(k + NS));
+            issue<Tg>(T, sgeo[stg], bufk, &bars[stg]);
+        }
         // ---- fold x: virtual columns onto the real column the padding maps them to
         if (geo.X.left || geo.X.right) {
             for (int gr = threadIdx.x; gr < nGR; gr += blockDim.x) {
@@ -179,46 +211,93 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
             __syncthreads();
         }
         // ---- pass y (adjoint along y) on the tile's real columns
-        const bool ypath_smem = geo.Y.left || geo.Y.right || !geo.Y.covered;
         float* sO = reinterpret_cast<float*>(bufk);  // the g tile is consumed
-        const int q = geo.qx0 + cl;
-        const bool col_ok = g2 < G2 && cl < geo.nqx;
-        const bool col_has = col_ok && q <= geo.X.vhi;
-        Tx* xcol = static_cast<Tx*>(T.gx) + (long long)geo.plane * Ny * Nx + q;
-        if (col_ok) {
-            float wf[S][SPAN];
+        Tg* const xplane = static_cast<Tg*>(T.gx) + (long long)geo.plane * Ny * Nx;
+        if constexpr (YV > 1) {
+            const int q = geo.qx0 + cy * YV;
+            const int nv = min(YV, geo.qx0 + geo.nqx - q);  // columns of this thread inside the tile
+            const int nh = min(nv, geo.X.vhi - q + 1);      // of which the intermediate holds values
+            if (g2 < G2 && nv > 0) {
+                const float* colp = sF + (q - fxb);
+                for (int ay = g2; ay < nAY; ay += G2) {
+                    const float* src = colp + ay * R * FXP;
+                    float2 acc[S][YV / 2];
 #pragma unroll
-            for (int u = 0; u < S; ++u)
+                    for (int u = 0; u < S; ++u)
 #pragma unroll
-                for (int qq = 0; qq < SPAN; ++qq) wf[u][qq] = sWFy[u * SPAN + qq];
-            const int fcol = q - fxb;
-            for (int ay = g2; ay < nAY; ay += G2) {
-                float v[SPAN];
-                if (col_has) {
-                    const float* src = sF + ay * R * FXP + fcol;
+                        for (int h = 0; h < YV / 2; ++h) acc[u][h] = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int qq = 0; qq < SPAN; ++qq) v[qq] = src[qq * FXP];
-                } else {
+                    for (int qq = 0; qq < SPAN; ++qq) {
+                        float v[YV];
+                        ldsv<YV>(src + qq * FXP, v);
+                        if (nh < YV) {
 #pragma unroll
-                    for (int qq = 0; qq < SPAN; ++qq) v[qq] = 0.f;
+                            for (int k = 0; k < YV; ++k) v[k] = k < nh ? v[k] : 0.f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < S; ++u)
+#pragma unroll
+                            for (int h = 0; h < YV / 2; ++h)
+                                acc[u][h] = __ffma2_rn(HOLD_Y ? wy[HOLD_Y ? u : 0][HOLD_Y ? qq : 0] : sWY2[u * SPAN + qq],
+                                                       make_float2(v[2 * h], v[2 * h + 1]), acc[u][h]);
+                    }
+                    const int vb = (geo.Y.alo + ay) * S + JY.lo_out;
+#pragma unroll
+                    for (int u = 0; u < S; ++u) {
+                        const int vr = vb + u;
+                        if (vr < geo.Y.vlo || vr > geo.Y.vhi) continue;
+                        float o[YV];
+#pragma unroll
+                        for (int h = 0; h < YV / 2; ++h) o[2 * h] = acc[u][h].x, o[2 * h + 1] = acc[u][h].y;
+                        if (ypath_smem) {
+                            float* p = sO + (vr - geo.Y.vlo) * QX + cy * YV;
+                            if (nv == YV) storev(p, o, YV);
+                            else for (int k = 0; k < nv; ++k) p[k] = o[k];
+                        } else {
+                            storev(xplane + (long long)vr * Nx + q, o, nv);
+                        }
+                    }
                 }
-                const int vb = (geo.Y.alo + ay) * S + JY.lo_out;
+            }
+        } else {
+            const int q = geo.qx0 + cl;
+            const bool col_ok = g3 < G3 && cl < geo.nqx;
+            const bool col_has = col_ok && q <= geo.X.vhi;
+            if (col_ok) {
+                float wf[S][SPAN];
 #pragma unroll
-                for (int u = 0; u < S; ++u) {
-                    const int vr = vb + u;
-                    if (vr < geo.Y.vlo || vr > geo.Y.vhi) continue;
-                    float acc = 0.f;
+                for (int u = 0; u < S; ++u)
 #pragma unroll
-                    for (int qq = 0; qq < SPAN; ++qq) acc = fmaf(wf[u][qq], v[qq], acc);
-                    if (ypath_smem) sO[(vr - geo.Y.vlo) * QX + cl] = acc;
-                    else store_out(xcol + (long long)vr * Nx, acc);
+                    for (int qq = 0; qq < SPAN; ++qq) wf[u][qq] = sWFy[u * SPAN + qq];
+                for (int ay = g3; ay < nAY; ay += G3) {
+                    float v[SPAN];
+                    if (col_has) {
+                        const float* src = sF + ay * R * FXP + (q - fxb);
+#pragma unroll
+                        for (int qq = 0; qq < SPAN; ++qq) v[qq] = src[qq * FXP];
+                    } else {
+#pragma unroll
+                        for (int qq = 0; qq < SPAN; ++qq) v[qq] = 0.f;
+                    }
+                    const int vb = (geo.Y.alo + ay) * S + JY.lo_out;
+#pragma unroll
+                    for (int u = 0; u < S; ++u) {
+                        const int vr = vb + u;
+                        if (vr < geo.Y.vlo || vr > geo.Y.vhi) continue;
+                        float acc = 0.f;
+#pragma unroll
+                        for (int qq = 0; qq < SPAN; ++qq) acc = fmaf(wf[u][qq], v[qq], acc);
+                        if (ypath_smem) sO[(vr - geo.Y.vlo) * QX + cl] = acc;
+                        else store_out(xplane + (long long)vr * Nx + q, acc);
+                    }
                 }
             }
         }
         if (ypath_smem) {
             __syncthreads();
-            if (col_ok) {
-                for (int qy = geo.qy0 + g2; qy < geo.qy0 + geo.nqy; qy += G2) {
+            if (g3 < G3 && cl < geo.nqx) {
+                Tg* xcol = xplane + geo.qx0 + cl;
+                for (int qy = geo.qy0 + g3; qy < geo.qy0 + geo.nqy; qy += G3) {
                     float acc = (qy >= geo.Y.vlo && qy <= geo.Y.vhi) ? sO[(qy - geo.Y.vlo) * QX + cl] : 0.f;
                     if (geo.Y.left || geo.Y.right) {
                         const int l1 = min(geo.Y.vhi, -1), r0 = max(geo.Y.vlo, Ny);
@@ -232,10 +311,9 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
             }
         }
         __syncthreads();  // sF and this stage are free again
-        if (threadIdx.x == 0 && tile + NS < tile_end) {
-            sgeo[stg] = dx_walk_geo(T, walk);
+        if (!early && threadIdx.x == 0 && k + NS < ntile) {
+            sgeo[stg] = dx_geo(T, tile_of(k + NS));
             issue<Tg>(T, sgeo[stg], bufk, &bars[stg]);
-            dx_walk_next(T, walk);
         }
         if (++stg == NS) {
             stg = 0;
@@ -244,25 +322,35 @@ __global__ void __launch_bounds__(256, 4) fcfs_bwd_dx2d_rs(const __grid_constant
     }
 }
 
+template <int S, int SPAN, int VW, typename Tg, int YV>
+cudaError_t launch_rs(const TmaDxParams& T, cudaStream_t st) {
+    const size_t smem = (size_t)T.bar_off + 8 * T.stages;
+    auto k = fcfs_bwd_dx2d_rs<S, SPAN, VW, Tg, YV>;
+    int sms = 0, per_sm = 0;
+    cudaError_t e = resident_ctas((const void*)k, T.threads, smem, &sms, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
+    k<<<(unsigned)grid, T.threads, smem, st>>>(T);
+    return cudaGetLastError();
+}
+
 template <int S, int SPAN, int VW, typename Tg>
 cudaError_t run_rs(const TmaDxParams& T, cudaStream_t st) {
-    constexpr int SPANX = (SPAN + VW - 1) / VW * VW;
+    constexpr int VP = VW > 2 ? VW : 2;
+    constexpr int SPANX = (SPAN + VP - 1) / VP * VP;
     // measured: the variant pays off when the x pass can own whole windows
     // without bank conflicts and the weight rows stay small; otherwise the
     // per-output kernel is faster (and wider rows are not instantiated)
     if constexpr (S * SPANX > 40) {
         return cudaErrorInvalidValue;
     } else {
-        const size_t smem = (size_t)T.bar_off + 8 * T.stages;
-        auto k = fcfs_bwd_dx2d_rs<S, SPAN, VW, Tg, Tg, true>;
-        if (T.WAcap > T.threads) return cudaErrorInvalidValue;
-        int sms = 0, per_sm = 0;
-        cudaError_t e = resident_ctas((const void*)k, T.threads, smem, &sms, &per_sm);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
-        k<<<(unsigned)grid, T.threads, smem, st>>>(T);
-        return cudaGetLastError();
+        if (T.WAcap > T.threads || T.QX % 4 != 0) return cudaErrorInvalidValue;
+        // y pass vector width: rows of gx a multiple of YV elements and the base aligned to YV elements
+        const int Nx = T.aj[2].n_x;
+        const uintptr_t gx = (uintptr_t)T.gx;
+        if (Nx % 4 == 0 && gx % (4 * sizeof(Tg)) == 0) return launch_rs<S, SPAN, VW, Tg, 4>(T, st);
+        return launch_rs<S, SPAN, VW, Tg, 1>(T, st);
     }
 }
 

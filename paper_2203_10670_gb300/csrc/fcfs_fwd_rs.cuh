@@ -83,28 +83,27 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd2d_rs(const __grid_constant__ 
         s_abort = 0;
     }
     __syncthreads();
-    const int ntiles = (int)T.ntiles;
-    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-    int tile = blockIdx.x * per;
-    const int tile_end = min(ntiles, tile + per);
-    if (tile >= tile_end) return;
+    const TileDeal deal = deal_tiles((int)T.ntiles, T.chunk);
+    const int ntile = deal.n;
+    if (ntile <= 0) return;
+    // two tiles in flight from the start; each later copy starts once a tile's x pass has read its buffer
     if (threadIdx.x == 0) {
-        sgeo[0] = tile_geo(T, tile);
+        sgeo[0] = tile_geo(T, deal.tile(0));
         issue_tile<Tin>(T, sgeo[0], buf0, &bars[0]);
+        if (ntile > 1) {
+            sgeo[1] = tile_geo(T, deal.tile(1));
+            issue_tile<Tin>(T, sgeo[1], buf1, &bars[1]);
+        }
     }
     const bool learn = AX.learn || AY.learn;
     int cur_c = -1;
-    for (int k = 0; tile < tile_end; ++k, ++tile) {
+    for (int k = 0; k < ntile; ++k) {
         Tin* buf = (k & 1) ? buf1 : buf0;
-        if (threadIdx.x == 0 && tile + 1 < tile_end) {
-            sgeo[(k + 1) & 1] = tile_geo(T, tile + 1);
-            issue_tile<Tin>(T, sgeo[(k + 1) & 1], (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
-        }
         if (!mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma)) s_abort = 1;
         __syncthreads();
         if (s_abort) {  // uniform: read after the barrier; this tile's and the prefetched copy in flight
             if (threadIdx.x == 0)
-                drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), tile + 1 < tile_end ? 2 : 1, &g_status_fwd_tma);
+                drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), k + 1 < ntile ? 2 : 1, &g_status_fwd_tma);
             return;
         }
         const TileGeo geo = sgeo[k & 1];
@@ -171,6 +170,11 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd2d_rs(const __grid_constant__ 
             }
         }
         __syncthreads();
+        // this tile's buffer is read: the copy two tiles ahead goes into it
+        if (threadIdx.x == 0 && k + 2 < ntile) {
+            sgeo[k & 1] = tile_geo(T, deal.tile(k + 2));
+            issue_tile<Tin>(T, sgeo[k & 1], buf, &bars[k & 1]);
+        }
 
         // ---- pass y: VW columns x all R phases of a window per thread
         const int oxy = cy * VW;

@@ -144,43 +144,6 @@ __device__ __forceinline__ void fix_edges(const TmaFwdParams& T, const TileGeo& 
     }
 }
 
-// Stores of n <= 4 adjacent outputs (the caller guarantees VW-element alignment).
-__device__ __forceinline__ void storev(float* p, const float* a, int n) {
-    if (n == 4) *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
-    else if (n == 2) *reinterpret_cast<float2*>(p) = make_float2(a[0], a[1]);
-    else for (int i = 0; i < n; ++i) p[i] = a[i];
-}
-__device__ __forceinline__ void storev(__nv_bfloat16* p, const float* a, int n) {
-    if (n == 4) {
-        __nv_bfloat162 lo = __floats2bfloat162_rn(a[0], a[1]), hi = __floats2bfloat162_rn(a[2], a[3]);
-        uint2 u;
-        u.x = *reinterpret_cast<uint32_t*>(&lo);
-        u.y = *reinterpret_cast<uint32_t*>(&hi);
-        *reinterpret_cast<uint2*>(p) = u;
-    } else if (n == 2) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a[0], a[1]);
-    } else {
-        for (int i = 0; i < n; ++i) p[i] = __float2bfloat16_rn(a[i]);
-    }
-}
-
-template <int VW>
-__device__ __forceinline__ void ldsv(const float* p, float* v) {
-    if (VW == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        v[0] = q.x;
-        v[1] = q.y;
-        v[2] = q.z;
-        v[3] = q.w;
-    } else if (VW == 2) {
-        const float2 q = *reinterpret_cast<const float2*>(p);
-        v[0] = q.x;
-        v[1] = q.y;
-    } else {
-        v[0] = *p;
-    }
-}
-
 // VW: the y pass handles VW adjacent output columns per thread (VW-wide shared
 // loads and global stores); VW > 1 needs tile width and output row length
 // multiples of VW.  The CTA size (256 or 512 threads) is a plan parameter.
@@ -223,32 +186,29 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ Tm
     }
     __syncthreads();
 
-    // each CTA owns a contiguous run of tiles (same plane for many tiles in a row);
     // thread 0 computes each tile's geometry once and shares it in shared memory
-    const int ntiles = (int)T.ntiles;
-    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-    int tile = blockIdx.x * per;
-    const int tile_end = min(ntiles, tile + per);
-    if (tile >= tile_end) return;
+    const TileDeal deal = deal_tiles((int)T.ntiles, T.chunk);
+    const int ntile = deal.n;
+    if (ntile <= 0) return;
+    // two tiles in flight from the start; each later copy starts once a tile's x pass has read its buffer
     if (threadIdx.x == 0) {
-        sgeo[0] = tile_geo(T, tile);
+        sgeo[0] = tile_geo(T, deal.tile(0));
         issue_tile<Tin>(T, sgeo[0], buf0, &bars[0]);
+        if (ntile > 1) {
+            sgeo[1] = tile_geo(T, deal.tile(1));
+            issue_tile<Tin>(T, sgeo[1], buf1, &bars[1]);
+        }
     }
     const bool learn = AX.learn || AY.learn;
     int cur_c = -1;
     float wxr[NT];
-    for (int k = 0; tile < tile_end; ++k, ++tile) {
+    for (int k = 0; k < ntile; ++k) {
         Tin* buf = (k & 1) ? buf1 : buf0;
-        // prefetch the next tile into the other buffer (its last reader passed the barrier below)
-        if (threadIdx.x == 0 && tile + 1 < tile_end) {
-            sgeo[(k + 1) & 1] = tile_geo(T, tile + 1);
-            issue_tile<Tin>(T, sgeo[(k + 1) & 1], (k & 1) ? buf0 : buf1, &bars[(k + 1) & 1]);
-        }
         if (!mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma)) s_abort = 1;
         __syncthreads();
         if (s_abort) {  // uniform: read after the barrier; this tile's and the prefetched copy in flight
             if (threadIdx.x == 0)
-                drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), tile + 1 < tile_end ? 2 : 1, &g_status_fwd_tma);
+                drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), k + 1 < ntile ? 2 : 1, &g_status_fwd_tma);
             return;
         }  // TMA data and this tile's geometry visible to all
         const TileGeo geo = sgeo[k & 1];
@@ -284,6 +244,11 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ Tm
             }
         }
         __syncthreads();
+        // this tile's buffer is read: the copy two tiles ahead goes into it
+        if (threadIdx.x == 0 && k + 2 < ntile) {
+            sgeo[k & 1] = tile_geo(T, deal.tile(k + 2));
+            issue_tile<Tin>(T, sgeo[k & 1], buf, &bars[k & 1]);
+        }
 
         // ---- pass y: thread = (VW columns, phase); outputs at pixel-shuffled positions
         const int gox = geo.ix0 * AX.r + oxy;

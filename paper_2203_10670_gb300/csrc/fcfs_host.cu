@@ -915,21 +915,27 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
     if (T->rs_vw > 1 && ((T->aj[2].lo_in % T->rs_vw) + T->rs_vw) % T->rs_vw != 0) T->rs_vw = 0;
     rs_ok = rs_ok && T->rs_vw > 0;
     T->rs_span = rs_ok ? true_span(T->aj[2]) : 0;
-    // a vector-loading x pass reads the span rounded up to VW samples from each window start
-    const int spanx = rs_ok && T->rs_vw > 1 ? (T->rs_span + T->rs_vw - 1) / T->rs_vw * T->rs_vw : 0;
+    // the x pass reads the span rounded up to VW samples (at least a pair) from each window start
+    const int vp = std::max(T->rs_vw, 2);
+    const int spanx = rs_ok ? (T->rs_span + vp - 1) / vp * vp : 0;
     for (int it = 0; it < 8; ++it) {
         // capacities over every tile position of each axis
-        int vx = 1, vy = 1, gw = 1, gh = 1, wa = 1;
+        int vx = 1, vy = 1, gw = 1, gh = 1, wa = 1, fxp = 1;
         for (int q0 = 0; q0 < Nx; q0 += T->QX) {
             const AxRange R = ax_range(T->aj[2], d->pad, q0, std::min(Nx, q0 + T->QX) - 1);
             vx = std::max(vx, R.vhi - R.vlo + 1);
             if (R.ahi >= R.alo) {
                 gw = std::max(gw, (R.ahi - R.alo) * T->aj[2].r + std::max(T->aj[2].span, spanx));
                 wa = std::max(wa, R.ahi - R.alo + 1);
+                // register-blocked layout: the windows' outputs start up to 3 columns in, and the
+                // y pass reads the tile's QX columns from its first real column
+                const int fxw = R.alo * T->aj[2].s + T->aj[2].lo_out;
+                fxp = std::max(fxp, 3 + (R.ahi - R.alo + 1) * T->aj[2].s);
+                fxp = std::max(fxp, 3 + q0 - fxw + T->QX);
             }
         }
         T->WAcap = wa;
-        T->FXP = std::max(vx, wa * T->aj[2].s);
+        T->FXP = rs_ok ? (std::max(vx, fxp) + 3) / 4 * 4 : std::max(vx, wa * T->aj[2].s);
         for (int q0 = 0; q0 < Ny; q0 += T->QY) {
             const AxRange R = ax_range(T->aj[1], d->pad, q0, std::min(Ny, q0 + T->QY) - 1);
             vy = std::max(vy, R.vhi - R.vlo + 1);
@@ -960,6 +966,9 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
     T->qtiles_x = (Nx + T->QX - 1) / T->QX;
     T->qtiles_y = (Ny + T->QY - 1) / T->QY;
     T->ntiles = (long long)T->qtiles_x * T->qtiles_y * d->n * d->c;
+    // tiles dealt one at a time round-robin (balanced edge tiles, shared halos in L2); one run per
+    // CTA for per-channel weights, which are restaged at every change of channel
+    T->chunk = B.ax[1].learn || B.ax[2].learn ? 0 : 1;
     if (T->ntiles >= (1LL << 31)) return -1;
     T->gy = gy;
     T->gx = gx;
@@ -1493,6 +1502,7 @@ int prepare_tma(const fcfs_desc* d, const FwdParams& P, TmaFwdParams* T, int thr
     if (P.OX > 256) return fail(FCFS_ERR_UNSUPPORTED, "tile wider than the CTA");
     T->ntiles = (long long)P.tiles_x * P.tiles_y * P.planes;
     if (T->ntiles >= (1LL << 31)) return fail(FCFS_ERR_UNSUPPORTED, "too many tiles");
+    T->chunk = P.ax[1].learn || P.ax[2].learn ? 0 : 1;
     T->threads = threads > 0 ? threads : 256;
     if (P.OX > T->threads) return fail(FCFS_ERR_UNSUPPORTED, "tile wider than the CTA");
     const cuuint64_t W = (cuuint64_t)P.ax[2].n_in, H = (cuuint64_t)P.ax[1].n_in;

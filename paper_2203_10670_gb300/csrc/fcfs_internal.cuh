@@ -136,6 +136,7 @@ struct TmaFwdParams {
     int bar_off;       // byte offset of the two mbarriers (16-byte aligned)
     int threads;       // CTA size
     long long ntiles;  // tiles_x * tiles_y * planes (< 2^31)
+    int chunk;         // tiles per chunk dealt round-robin to the CTAs (0: one contiguous run per CTA)
 };
 
 // Adjoint of one axis as a forward-like polyphase operator: window a of the
@@ -177,6 +178,7 @@ struct TmaDxParams {
     // axes), adjoint windows per tile row, pitch of the window-relative Fx
     int rs_span, WAcap, FXP;
     int rs_vw;  // register-blocked x pass: elements per vector load of a window (1 = scalar loads)
+    int chunk;  // register-blocked kernel: tiles per chunk dealt round-robin to the CTAs (0: one run per CTA)
 };
 
 // Bulk-copy staged input-gradient parameters (3D): the 2D tile of real
@@ -333,6 +335,43 @@ __device__ __forceinline__ void load_vec(const Tg* p, float* v) {
 
 __device__ __forceinline__ void store_f(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store_f(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// Stores of n <= 4 adjacent outputs (the caller guarantees VW-element alignment).
+__device__ __forceinline__ void storev(float* p, const float* a, int n) {
+    if (n == 4) *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+    else if (n == 2) *reinterpret_cast<float2*>(p) = make_float2(a[0], a[1]);
+    else for (int i = 0; i < n; ++i) p[i] = a[i];
+}
+__device__ __forceinline__ void storev(__nv_bfloat16* p, const float* a, int n) {
+    if (n == 4) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(a[0], a[1]), hi = __floats2bfloat162_rn(a[2], a[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&lo);
+        u.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(p) = u;
+    } else if (n == 2) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a[0], a[1]);
+    } else {
+        for (int i = 0; i < n; ++i) p[i] = __float2bfloat16_rn(a[i]);
+    }
+}
+
+template <int VW>
+__device__ __forceinline__ void ldsv(const float* p, float* v) {
+    if (VW == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else if (VW == 2) {
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        v[0] = *p;
+    }
+}
 
 __host__ __device__ inline int imin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }

@@ -94,4 +94,36 @@ __device__ __forceinline__ void drain_ring(uint64_t* bars, int S, int stg, uint3
     }
 }
 
+
+// The tiles one CTA of a persistent grid takes: chunks of `chunk` consecutive
+// tiles dealt round-robin over the grid (the costlier edge tiles spread over
+// all CTAs and neighbouring tiles run at the same time, sharing their halos
+// in L2), or one contiguous run per CTA when chunk is 0 (fewer changes of
+// plane, for per-channel weights).  k-th tile of this CTA: tile(k), k < n.
+struct TileDeal {
+    int b, G, per, chunk, n;
+    __device__ __forceinline__ int tile(int k) const {
+        if (chunk == 0) return b * per + k;
+        const int j = k / chunk;
+        return (b + j * G) * chunk + (k - j * chunk);
+    }
+};
+
+__device__ __forceinline__ TileDeal deal_tiles(int ntiles, int chunk) {
+    TileDeal d;
+    d.b = blockIdx.x;
+    d.G = gridDim.x;
+    d.per = (ntiles + d.G - 1) / d.G;
+    d.chunk = chunk;
+    if (chunk <= 0) {
+        d.chunk = 0;
+        d.n = max(0, min(ntiles, (d.b + 1) * d.per) - d.b * d.per);
+    } else {
+        const int nch = (ntiles + chunk - 1) / chunk;
+        d.n = nch > d.b ? ((nch - 1 - d.b) / d.G + 1) * chunk : 0;
+        if (nch > d.b && (nch - 1 - d.b) % d.G == 0) d.n -= nch * chunk - ntiles;  // the short last chunk
+    }
+    return d;
+}
+
 }  // namespace fcfs

@@ -204,18 +204,20 @@ def test_batch_submission(F):
 def test_cancel_queued_and_running_requests(F):
     # a client that gives up on requests: queued ones leave at once, running ones stop receiving
     # tiles; every id is still reported once, the rest of the stream completes normally
-    reqs = _requests(24, 7, lo=400, hi=800)
-    # one request admitted at a time, two tiles per step: the first is running, the rest queued
+    # a large first request (thousands of two-tile steps) keeps the others queued behind it while
+    # the client cancels: one request admitted at a time
+    big = (inputs.uint8_pixels((1, 3, 2048, 2048), 4321, device="cuda"), (3, 2), 2)
+    reqs = [big] + _requests(23, 7, lo=400, hi=800)
     with F.Server(1 << 30, max_inflight=1, tile_budget_per_step=2, auto_release=False) as sv:
         ids = [sv.submit(x, ratio, m) for x, ratio, m in reqs]
-        victims = set()
-        for rid in [ids[0]] + ids[1::3]:
-            try:
-                sv.cancel(rid)
-                victims.add(rid)
-            except F.FCFSError:  # it finished before the cancel reached it
-                pass
-        assert len(victims) >= len(ids[1::3])
+        victims = set(ids[1::3])
+        for rid in ids[1::3]:
+            sv.cancel(rid)  # queued: leaves at once
+        try:
+            sv.cancel(ids[0])  # running (or, on a very fast device, already finished)
+            victims.add(ids[0])
+        except F.FCFSError:
+            pass
         with pytest.raises(F.FCFSError):
             sv.cancel(10 ** 9)  # unknown id
         sv.drain(120_000)
