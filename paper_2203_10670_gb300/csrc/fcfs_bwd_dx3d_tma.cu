@@ -77,13 +77,13 @@ struct CursorDx3 {
 };
 
 template <typename Tg>
-__device__ __forceinline__ void issue_next(const TmaDx3Params& T, CursorDx3& c, int t_end, unsigned char* smem,
+__device__ __forceinline__ void issue_next(const TmaDx3Params& T, CursorDx3& c, const TileDeal& d, unsigned char* smem,
                                            uint64_t* bars) {
-    if (c.tile >= t_end) return;
+    if (c.tile >= d.n) return;
     if (c.n > 0 && ++c.gd > c.g.g_last) {
         do {
-            if (++c.tile >= t_end) return;
-            c.g = dx3_geo(T, c.tile);
+            if (++c.tile >= d.n) return;
+            c.g = dx3_geo(T, d.tile(c.tile));
         } while (c.g.g_last < c.g.g_first);
         c.gd = c.g.g_first;
     }
@@ -140,20 +140,19 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constan
     const int Nx = JX.n_x, Ny = JY.n_x, Nd = JD.n_x;
     const int ringn = JD.span;
 
-    const int per = (T.ntiles + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per, t_end = min(T.ntiles, t_begin + per);
-    if (t_begin >= t_end) return;
+    const TileDeal deal = deal_tiles(T.ntiles, T.chunk);
+    if (deal.n <= 0) return;
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
         s_abort = 0;
-        cur.tile = t_begin;
-        cur.g = dx3_geo(T, t_begin);
-        while (cur.g.g_last < cur.g.g_first && ++cur.tile < t_end) cur.g = dx3_geo(T, cur.tile);
+        cur.tile = 0;
+        cur.g = dx3_geo(T, deal.tile(0));
+        while (cur.g.g_last < cur.g.g_first && ++cur.tile < deal.n) cur.g = dx3_geo(T, deal.tile(cur.tile));
         cur.gd = cur.g.g_first;
         cur.n = 0;
         cur.k = 0;
-        for (int k = 0; k < S; ++k) issue_next<Tg>(T, cur, t_end, smem_raw, bars);
+        for (int k = 0; k < S; ++k) issue_next<Tg>(T, cur, deal, smem_raw, bars);
     }
     __syncthreads();
     const bool learn = T.ax[0].learn || T.ax[1].learn || T.ax[2].learn;
@@ -161,8 +160,8 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constan
     int stg = 0;         // stage of the current job
     uint32_t phase = 0;  // its barrier phase
     int consumed = 0;    // jobs taken so far (cur.n were issued)
-    for (int tile = t_begin; tile < t_end; ++tile) {
-        const Dx3Geo gt = dx3_geo(T, tile);
+    for (int kt = 0; kt < deal.n; ++kt) {
+        const Dx3Geo gt = dx3_geo(T, deal.tile(kt));
         Tx* xpl = static_cast<Tx*>(T.gx) + (long long)gt.plane * Nd * Ny * Nx;
         const bool col_ok = active && cl < gt.nqx;
         if (gt.g_last < gt.g_first) {
@@ -323,7 +322,7 @@ __global__ void __launch_bounds__(256, 2) fcfs_bwd_dx3d_tma(const __grid_constan
                 ++ad;
             }
             __syncthreads();  // the ring slot, sF and this stage are free again
-            if (threadIdx.x == 0) issue_next<Tg>(T, cur, t_end, smem_raw, bars);
+            if (threadIdx.x == 0) issue_next<Tg>(T, cur, deal, smem_raw, bars);
             if (++rslot == ringn) rslot = 0;
             if (++stg == S) {
                 stg = 0;

@@ -52,24 +52,17 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
     const bool active = gq < G;
     const int Nx = JX.n_x, Ny = JY.n_x;
 
-    // each CTA owns a contiguous run of tiles (same plane for many tiles in a row)
-    const int ntiles = (int)T.ntiles;
-    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-    int tile = blockIdx.x * per;
-    const int tile_end = min(ntiles, tile + per);
-    if (tile >= tile_end) return;
+    const TileDeal deal = deal_tiles((int)T.ntiles, T.chunk);
+    if (deal.n <= 0) return;
     // geometry of the tile in each stage, computed once by the thread that issues its copy
     __shared__ DxGeo sgeo[4];
-    __shared__ DxWalk walk;  // the next tile to issue
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
         s_abort = 0;
-        dx_walk_init(T, walk, tile);
-        for (int k = 0; k < S && tile + k < tile_end; ++k) {
-            sgeo[k] = dx_walk_geo(T, walk);
+        for (int k = 0; k < S && k < deal.n; ++k) {
+            sgeo[k] = dx_geo(T, deal.tile(k));
             issue<Tg>(T, sgeo[k], smem_raw + k * T.buf_bytes, &bars[k]);
-            dx_walk_next(T, walk);
         }
     }
     __syncthreads();
@@ -77,13 +70,13 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
     int cur_c = -1;
     int stg = 0;
     uint32_t phase = 0;
-    for (; tile < tile_end; ++tile) {
+    for (int kt = 0; kt < deal.n; ++kt) {
         unsigned char* const bufk = smem_raw + stg * T.buf_bytes;
         // one warp waits for the copy; the barrier releases the others
         if (threadIdx.x < 32 && !mbar_wait(&bars[stg], phase, &g_status_bwd_tma)) s_abort = 1;
         __syncthreads();
         if (s_abort) {
-            if (threadIdx.x == 0) drain_ring(bars, S, stg, phase, min(S, tile_end - tile), &g_status_bwd_tma);
+            if (threadIdx.x == 0) drain_ring(bars, S, stg, phase, min(S, deal.n - kt), &g_status_bwd_tma);
             return;
         }
         const DxGeo geo = sgeo[stg];
@@ -188,10 +181,9 @@ __global__ void __launch_bounds__(256) fcfs_bwd_dx2d_tma(const __grid_constant__
             }
         }
         __syncthreads();  // sF, the tables and this stage are free again
-        if (threadIdx.x == 0 && tile + S < tile_end) {
-            sgeo[stg] = dx_walk_geo(T, walk);
+        if (threadIdx.x == 0 && kt + S < deal.n) {
+            sgeo[stg] = dx_geo(T, deal.tile(kt + S));
             issue<Tg>(T, sgeo[stg], bufk, &bars[stg]);
-            dx_walk_next(T, walk);
         }
         if (++stg == S) {
             stg = 0;

@@ -51,59 +51,6 @@ __device__ __forceinline__ DxGeo dx_geo(const TmaDxParams& T, int tile) {
     return g;
 }
 
-// Tile geometry walked incrementally along a CTA's contiguous run of tiles
-// (tx fastest, then ty, then plane): no integer division per tile except
-// the x range; the y range is recomputed only when the tile row changes.
-// Kept in shared memory by the thread that issues the copies.
-struct DxWalk {
-    int tx, ty, plane, c;
-    AxRange Y;
-};
-
-__device__ __forceinline__ void dx_walk_y(const TmaDxParams& T, DxWalk& w) {
-    const int qy0 = w.ty * T.QY;
-    w.Y = ax_range(T.aj[1], T.pad, qy0, qy0 + min(T.QY, T.aj[1].n_x - qy0) - 1);
-}
-
-__device__ __forceinline__ void dx_walk_init(const TmaDxParams& T, DxWalk& w, int tile) {
-    const int txy = T.qtiles_x * T.qtiles_y;
-    w.plane = tile / txy;
-    const int rem = tile - w.plane * txy;
-    w.ty = rem / T.qtiles_x;
-    w.tx = rem - w.ty * T.qtiles_x;
-    w.c = w.plane % T.C;
-    dx_walk_y(T, w);
-}
-
-__device__ __forceinline__ void dx_walk_next(const TmaDxParams& T, DxWalk& w) {
-    if (++w.tx < T.qtiles_x) return;
-    w.tx = 0;
-    if (++w.ty == T.qtiles_y) {
-        w.ty = 0;
-        ++w.plane;
-        if (++w.c == T.C) w.c = 0;
-    }
-    dx_walk_y(T, w);
-}
-
-// the same result as dx_geo for the walker's tile
-__device__ __forceinline__ DxGeo dx_walk_geo(const TmaDxParams& T, const DxWalk& w) {
-    DxGeo g;
-    g.plane = w.plane;
-    g.c = w.c;
-    g.qx0 = w.tx * T.QX;
-    g.qy0 = w.ty * T.QY;
-    g.nqx = min(T.QX, T.aj[2].n_x - g.qx0);
-    g.nqy = min(T.QY, T.aj[1].n_x - g.qy0);
-    g.X = ax_range(T.aj[2], T.pad, g.qx0, g.qx0 + g.nqx - 1);
-    g.Y = w.Y;
-    const int gx0 = g.X.alo * T.aj[2].r + T.aj[2].lo_in;
-    g.gx_al = gx0 & -T.align;  // align is a power of two: rounds toward minus infinity
-    g.xoff = gx0 - g.gx_al;
-    g.gy0 = g.Y.alo * T.aj[1].r + T.aj[1].lo_in;
-    return g;
-}
-
 template <typename Tg>
 __device__ __forceinline__ void issue(const TmaDxParams& T, const DxGeo& g, void* buf, uint64_t* bar) {
     fence_proxy_async_smem();

@@ -57,19 +57,18 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
     const bool act2 = g2 < G2;
     const int oxy = cy * VW;
 
-    const int per = (T.ntiles + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per, t_end = min(T.ntiles, t_begin + per);
-    if (t_begin >= t_end) return;
+    const TileDeal deal = deal_tiles(T.ntiles, T.chunk);
+    if (deal.n <= 0) return;
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
         s_abort = 0;
-        cur.tile = t_begin;
-        cur.g = geo3(T, t_begin);
+        cur.tile = 0;
+        cur.g = geo3(T, deal.tile(0));
         cur.p = cur.g.p_first;
         cur.n = 0;
         cur.k = 0;
-        for (int k = 0; k < S; ++k) issue_next<Tin>(T, cur, t_end, smem_raw, bars);
+        for (int k = 0; k < S; ++k) issue_next<Tin>(T, cur, deal, smem_raw, bars);
     }
     __syncthreads();
     const bool learn = AX.learn || AY.learn || AD.learn;
@@ -77,8 +76,8 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
     int k = 0;           // stage of the current job
     uint32_t phase = 0;  // its barrier phase
     int consumed = 0;    // jobs taken so far (cur.n were issued)
-    for (int tile = t_begin; tile < t_end; ++tile) {
-        const Geo3 geo = geo3(T, tile);
+    for (int kt = 0; kt < deal.n; ++kt) {
+        const Geo3 geo = geo3(T, deal.tile(kt));
         if (cur_c < 0 || (learn && geo.c != cur_c)) {
             // the previous tile ended with a barrier: no thread still reads the weights
             stage3<NT>(sWx, AX, geo.c);
@@ -199,7 +198,7 @@ __global__ void __launch_bounds__(256, 3) fcfs_fwd3d_rs(const __grid_constant__ 
                 ++idl;
             }
             __syncthreads();  // ring slots, sH and this stage are free again
-            if (threadIdx.x == 0) issue_next<Tin>(T, cur, t_end, smem_raw, bars);
+            if (threadIdx.x == 0) issue_next<Tin>(T, cur, deal, smem_raw, bars);
             if (++rslot == P.ring) rslot = 0;
             if (++k == S) {
                 k = 0;

@@ -115,21 +115,21 @@ __device__ __forceinline__ void stage3(float* dst, const AxisP& A, int c) {
 // Issue cursor of the job stream, kept by thread 0 in shared memory.
 struct Cursor3 {
     Geo3 g;     // geometry of the tile being issued
-    int tile;   // tile of the last issued job
+    int tile;   // this CTA's tile number (TileDeal index) of the last issued job
     int p;      // plane of the last issued job
     int n;      // jobs issued so far
     int k;      // stage of the next job to issue
 };
 
-// Issue the next job of the stream [t_begin, t_end) into stage n % stages.
+// Issue the next job of the stream over this CTA's tiles into stage n % stages.
 template <typename Tin>
-__device__ __forceinline__ void issue_next(const TmaFwd3Params& T, Cursor3& c, int t_end, unsigned char* smem,
+__device__ __forceinline__ void issue_next(const TmaFwd3Params& T, Cursor3& c, const TileDeal& d, unsigned char* smem,
                                            uint64_t* bars) {
-    if (c.tile >= t_end) return;
+    if (c.tile >= d.n) return;
     if (c.n > 0) {
         if (++c.p > c.g.p_last) {
-            if (++c.tile >= t_end) return;
-            c.g = geo3(T, c.tile);
+            if (++c.tile >= d.n) return;
+            c.g = geo3(T, d.tile(c.tile));
             c.p = c.g.p_first;
         }
     }

@@ -292,8 +292,176 @@ __global__ void __launch_bounds__(512) fcfs_fwd2d_tma(const __grid_constant__ Tm
     }
 }
 
+// K2, the one-tap forward (nearest, or a learnable one-tap layer) as a
+// direct copy: each output reads its source sample from the staged input tile
+// and VW outputs of a row (16 bytes) leave in one vector store; there is no
+// intermediate.  Every output is fmaf(wy, fmaf(wx, x, -0), -0), the two
+// roundings of the two-pass kernel (an exact copy for unit weights).  Used
+// for BF16 outputs.  Shared memory: the two staging buffers, the mbarriers,
+// the phase weights.
+template <typename Tout, int VW>
+__device__ __forceinline__ void store_row(Tout* p, const float* o, int n);
+template <>
+__device__ __forceinline__ void store_row<__nv_bfloat16, 8>(__nv_bfloat16* p, const float* o, int n) {
+    if (n == 8) {
+        uint4 u;
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(o[0], o[1]), h1 = __floats2bfloat162_rn(o[2], o[3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(o[4], o[5]), h3 = __floats2bfloat162_rn(o[6], o[7]);
+        u.x = *reinterpret_cast<uint32_t*>(&h0);
+        u.y = *reinterpret_cast<uint32_t*>(&h1);
+        u.z = *reinterpret_cast<uint32_t*>(&h2);
+        u.w = *reinterpret_cast<uint32_t*>(&h3);
+        *reinterpret_cast<uint4*>(p) = u;
+    } else {
+        for (int i = 0; i < n; ++i) p[i] = __float2bfloat16_rn(o[i]);
+    }
+}
+
+template <typename Tin, typename Tout, int VW>
+__global__ void __launch_bounds__(256) fcfs_copy2d_tma(const __grid_constant__ TmaFwdParams T) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ TileGeo sgeo[2];
+    __shared__ int s_abort;  // set when a bounded wait ran out: the CTA stops
+    const FwdParams& P = T.P;
+    const AxisP& AY = P.ax[1];
+    const AxisP& AX = P.ax[2];
+    Tin* buf0 = reinterpret_cast<Tin*>(smem_raw);
+    Tin* buf1 = reinterpret_cast<Tin*>(smem_raw + T.buf_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + 2 * T.buf_bytes);
+    float* sW = reinterpret_cast<float*>(smem_raw + 2 * T.buf_bytes + 16);  // x phases, then y phases
+    const int BW = T.BW, RX = AX.r, RY = AY.r;
+    // thread = VW adjacent output columns of the tile, row groups over the tile's output rows
+    const int NC = P.OX / VW;
+    const int G = blockDim.x / NC;
+    const int cx = threadIdx.x % NC, g = threadIdx.x / NC;
+    const int ox0 = cx * VW;
+    int sc[VW];  // source column of each of the thread's columns, from the tile's first window start
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+        const int ox = ox0 + v, i = ox / RX;
+        sc[v] = i * AX.s + AX.off[ox - i * RX];
+    }
+    // output row oyl of the tile = window iyl, phase jy; this thread's rows step by G
+    const int di = G / RY, dj = G - di * RY;
+    const int iy_start = g / RY, jy_start = g - iy_start * RY;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    const TileDeal deal = deal_tiles((int)T.ntiles, T.chunk);
+    const int ntile = deal.n;
+    if (ntile <= 0) return;
+    if (threadIdx.x == 0) {
+        sgeo[0] = tile_geo(T, deal.tile(0));
+        issue_tile<Tin>(T, sgeo[0], buf0, &bars[0]);
+        if (ntile > 1) {
+            sgeo[1] = tile_geo(T, deal.tile(1));
+            issue_tile<Tin>(T, sgeo[1], buf1, &bars[1]);
+        }
+    }
+    const bool learn = AX.learn || AY.learn;
+    int cur_c = -1;
+    float wx[VW];
+    bool unit = false;  // unit weights and no epilogue: the output is the sample itself
+    for (int k = 0; k < ntile; ++k) {
+        Tin* buf = (k & 1) ? buf1 : buf0;
+        if (!mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), &g_status_fwd_tma)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {
+            if (threadIdx.x == 0)
+                drain_ring(bars, 2, k & 1, (uint32_t)((k >> 1) & 1), k + 1 < ntile ? 2 : 1, &g_status_fwd_tma);
+            return;
+        }
+        const TileGeo geo = sgeo[k & 1];
+        if (cur_c < 0 || (learn && geo.c != cur_c)) {
+            for (int e = threadIdx.x; e < RX + RY; e += blockDim.x) {
+                const AxisP& A = e < RX ? AX : AY;
+                const int j = e < RX ? e : e - RX;
+                sW[e] = A.learn ? A.w[geo.c * A.w_cstride + j * A.nt_src] : A.wf[j * A.nt_src];
+            }
+            __syncthreads();
+            bool u = !epi_on(P.epi);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) {
+                const int ox = ox0 + v;
+                wx[v] = sW[ox - (ox / RX) * RX];
+                u = u && wx[v] == 1.f;
+            }
+            for (int j = 0; j < RY; ++j) u = u && sW[RX + j] == 1.f;
+            unit = __syncthreads_and(u);  // one path for the whole CTA
+            cur_c = geo.c;
+        }
+        if (geo.edge) fix_edges<Tin>(T, geo, buf);
+
+        const int ncol = min(geo.nwx * RX, AX.n_out - geo.ix0 * RX);  // valid output columns of the tile
+        const int nv = min(VW, ncol - ox0);
+        const int nrow = min(geo.nwy * RY, AY.n_out - geo.iy0 * RY);
+        if (g < G && nv > 0) {
+            const Tin* src = buf + geo.xoff;
+            Tout* yrow = static_cast<Tout*>(P.y) + (long long)geo.plane * AY.n_out * AX.n_out +
+                         (long long)geo.iy0 * RY * AX.n_out + geo.ix0 * RX + ox0;
+            int iyl = iy_start, jy = jy_start;
+            for (int oyl = g; oyl < nrow; oyl += G) {
+                const Tin* row = src + (iyl * AY.s + AY.off[jy]) * BW;
+                float o[VW];
+                if (unit) {
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) o[v] = to_f<Tin>(row[sc[v]]);
+                } else {
+                    const float wy = sW[RX + jy];
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) {
+                        float a = fmaf(wy, fmaf(wx[v], to_f<Tin>(row[sc[v]]), -0.f), -0.f);
+                        o[v] = epi_on(P.epi) ? epi_apply(P.epi, geo.c, a) : a;
+                    }
+                }
+                store_row<Tout, VW>(yrow + (long long)oyl * AX.n_out, o, nv);
+                iyl += di;
+                jy += dj;
+                if (jy >= RY) {
+                    jy -= RY;
+                    ++iyl;
+                }
+            }
+        }
+        __syncthreads();  // this buffer is read
+        if (threadIdx.x == 0 && k + 2 < ntile) {
+            sgeo[k & 1] = tile_geo(T, deal.tile(k + 2));
+            issue_tile<Tin>(T, sgeo[k & 1], buf, &bars[k & 1]);
+        }
+    }
+}
+
+// The direct one-tap copy when 16-byte output vectors fit the tile and the rows.
+template <typename Tin, typename Tout>
+cudaError_t run_copy(const TmaFwdParams& T, cudaStream_t st) {
+    constexpr int VW = 16 / sizeof(Tout);
+    const int no = T.P.ax[2].n_out;
+    if (T.P.OX % VW || no % VW || (uintptr_t)T.P.y % 16) return cudaErrorInvalidValue;
+    if (T.P.OX / VW > 256) return cudaErrorInvalidValue;
+    const size_t smem = 2 * (size_t)T.buf_bytes + 16 + 4 * (size_t)(T.P.ax[2].r + T.P.ax[1].r);
+    auto k = fcfs_copy2d_tma<Tin, Tout, VW>;
+    int sms = 0, per_sm = 0;
+    cudaError_t e = resident_ctas((const void*)k, 256, smem, &sms, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long grid = std::min<long long>(T.ntiles, (long long)sms * per_sm);
+    k<<<(unsigned)grid, 256, smem, st>>>(T);
+    return cudaGetLastError();
+}
+
 template <int NT, typename Tin, typename Tout>
 cudaError_t run(const TmaFwdParams& T, size_t smem, cudaStream_t st) {
+    // BF16 rows: the direct copy (measured 1.4x faster); FP32: the two passes, whose lanes read
+    // consecutive samples (the copy's per-thread column runs conflict in the shared-memory banks)
+    if constexpr (NT == 1 && std::is_same<Tout, __nv_bfloat16>::value) {
+        const cudaError_t e = run_copy<Tin, Tout>(T, st);
+        if (e != cudaErrorInvalidValue) return e;
+    }
     const int no = T.P.ax[2].n_out;
     const uintptr_t y = (uintptr_t)T.P.y;
     const bool v4 = T.P.OX % 4 == 0 && no % 4 == 0 && y % (4 * sizeof(Tout)) == 0;

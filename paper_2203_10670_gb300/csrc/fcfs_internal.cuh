@@ -200,6 +200,7 @@ struct TmaDx3Params {
     int buf_bytes, fx_off, ring_off, facc_off, w_off, tab_off, bar_off;
     int threads;
     int ntiles;
+    int chunk;  // tiles per chunk dealt round-robin to the CTAs (0: one contiguous run per CTA)
     const void* gy;
     void* gx;
 };
@@ -232,6 +233,7 @@ struct TmaFwd3Params {
     int buf_bytes, sh_off, ring_off, w_off, bar_off;
     int threads;
     int ntiles;
+    int chunk;  // tiles per chunk dealt round-robin to the CTAs (0: one contiguous run per CTA)
 };
 
 struct NearestParams {

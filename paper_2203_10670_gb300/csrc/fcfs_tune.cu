@@ -53,11 +53,18 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     // 3D: depth windows per tile as well (half, same, double the default)
     const int wd_scale[] = {2, 4, 8};
     for (int oxt : ox_targets)
+        for (int al = 0; al < 2; ++al)
         for (int oyt : oy_targets)
             for (int gm = 0; gm < 4; ++gm)
                 for (int ws : wd_scale) {
                     if (!is3d && ws != 4) continue;
-                    TileChoice t{std::max(1, oxt / P0.ax[2].r), std::max(1, oyt / ry), std::max(1, def.WD * ws / 4)};
+                    // al = 1: the width rounded down to a multiple of 8 outputs (16-byte BF16 stores)
+                    int wx = std::max(1, oxt / P0.ax[2].r);
+                    if (al) {
+                        while (wx > 1 && (wx * P0.ax[2].r) % 8) --wx;
+                        if ((wx * P0.ax[2].r) % 8 || wx == std::max(1, oxt / P0.ax[2].r)) continue;
+                    }
+                    TileChoice t{wx, std::max(1, oyt / ry), std::max(1, def.WD * ws / 4)};
                     t.tma = def.tma;
                     // TMA kernel: the second variant is the 512-thread CTA; gather kernel: thread groups
                     t.G = tma ? 0 : (gm == 0 ? def.G : (def.G == ry ? 1 : ry));
