@@ -441,6 +441,9 @@ def extras(fcfs, inputs, device, stream, peak, tune=True, checks=True):
     for name, (r, s), m in OPS:
         ax = [fcfs.Axis(r, s, m)] * 2
         y = torch.empty(fcfs.out_shape(shape, ax), device=device, dtype=torch.bfloat16)
+        if tune:  # BF16 plans are cached apart from the FP32 ones
+            db = fcfs.make_desc(shape, ax, fcfs.FCFS_BF16, fcfs.FCFS_BF16)
+            fcfs.fcfs_tune_forward(db, xb.data_ptr(), y.data_ptr(), stream.cuda_stream, 3)
         fcfs.resize(xb, ax, out=y)
         t = timed(lambda: fcfs.resize(xb, ax, out=y), steps, stream) / steps
         nb = xb.numel() * 2 + y.numel() * 2
@@ -482,6 +485,9 @@ def extras(fcfs, inputs, device, stream, peak, tune=True, checks=True):
     ax = [fcfs.Axis(5, 4, fcfs.BILINEAR, K, wts[0]), fcfs.Axis(5, 4, fcfs.BILINEAR, K, wts[1])]
     x3 = inputs.normal(s3, inputs.C3["seed"], device=device, dtype=torch.bfloat16)
     y3 = fcfs.resize(x3, ax)
+    if tune:
+        d3t = fcfs.make_desc(s3, ax, fcfs.FCFS_BF16, fcfs.FCFS_BF16)
+        fcfs.fcfs_tune_forward(d3t, x3.data_ptr(), y3.data_ptr(), stream.cuda_stream, 3)
     g3 = inputs.normal(tuple(y3.shape), inputs.C3["grad_seed"], device=device, dtype=torch.bfloat16)
     fcfs.resize_backward(x3, g3, ax, need_dx=True, need_dw=[True, True])
     tf = timed(lambda: fcfs.resize(x3, ax, out=y3), steps, stream) / steps
