@@ -4,6 +4,8 @@
 // the pixel-shuffled output positions (Sec. 3.1; Sec. 4 per axis).
 #pragma once
 
+#include <type_traits>
+
 #include "fcfs_internal.cuh"
 
 namespace fcfs {
@@ -41,6 +43,32 @@ __device__ __forceinline__ void load_tile(float* sIn, int pitch, const Tin* src_
             continue;
         }
         const Tin* src = src_plane + (long long)sy * W;
+        if constexpr (std::is_same<Tin, uint8_t>::value) {
+            if (inside_x) {
+                // bytes read as aligned 4-byte words (4x fewer load requests than byte loads); every
+                // word read holds at least one byte of the row segment, so it stays in a mapped page
+                const uintptr_t a = reinterpret_cast<uintptr_t>(src + col0);
+                const uint32_t* wp = reinterpret_cast<const uint32_t*>(a & ~(uintptr_t)3);
+                const int mis = (int)(a & 3);
+                const int nw = (mis + cols + 3) >> 2;
+                constexpr int U = 4;
+                for (int k0 = lane; k0 < nw; k0 += 32 * U) {
+                    uint32_t w[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) w[u] = k0 + 32 * u < nw ? __ldg(wp + k0 + 32 * u) : 0u;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int e0 = 4 * (k0 + 32 * u) - mis;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int e = e0 + b;
+                            if (e >= 0 && e < cols) dst[e] = (float)((w[u] >> (8 * b)) & 0xffu);
+                        }
+                    }
+                }
+                continue;
+            }
+        }
         if (inside_x) {
             const Tin* s0 = src + col0;
             constexpr int U = 8;

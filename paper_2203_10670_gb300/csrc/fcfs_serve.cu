@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "fcfs_fwd_tile.cuh"
+#include "fcfs_tma.cuh"
 #include "fcfs_host.h"
 #include "fcfs_sched.h"
 
@@ -26,13 +27,11 @@ namespace {
 
 constexpr int kServeThreads = 256;
 constexpr int kServeMaxSmem = 48 * 1024;  // four CTAs per SM (the register limit too)
+// work items dealt to the CTAs in chunks of four consecutive items (tiles of one request,
+// mostly): tile costs differ across requests, and contiguous runs left SMs idle at the end
+// of a step (75 -> 97 Gpix/s on the mixed stream)
+constexpr int kServeChunk = 4;
 
-// Device parameter slot of one admitted request.
-struct ServeSlot {
-    FwdParams P;
-    int din;  // fcfs_dtype of x
-    int nt;   // tap template (1 nearest, 2 bilinear, 4 bicubic)
-};
 
 struct WorkItem {
     int slot;
@@ -58,6 +57,63 @@ struct ServeReq {
 struct ServeTile {
     int plane, ix0, iy0, nwx, nwy, cols, rows, col0, row0;
 };
+
+// Device parameter slot of one admitted request: the compact record the
+// kernel reads (scalars, phase taps padded to four, phase offsets), written
+// on the host at admission, then the full forward parameters of the plan.
+struct ServeSlot {
+    ServeReq q;
+    float wx[kMaxR * 4], wy[kMaxR * 4];
+    short offx[kMaxR], offy[kMaxR];
+    FwdParams P;
+    int din;  // fcfs_dtype of x
+    int nt;   // tap template (1 nearest, 2 bilinear, 4 bicubic)
+};
+
+// The compact record of a slot from its forward parameters (y set).
+void fill_serve_rec(ServeSlot& S) {
+    const AxisP& AX = S.P.ax[2];
+    const AxisP& AY = S.P.ax[1];
+    ServeReq& q = S.q;
+    q.x = S.P.x;
+    q.y = S.P.y;
+    q.din = S.din;
+    q.nt = S.nt;
+    q.H = AY.n_in;
+    q.W = AX.n_in;
+    q.Ho = AY.n_out;
+    q.Wo = AX.n_out;
+    q.rx = AX.r;
+    q.sx = AX.s;
+    q.ry = AY.r;
+    q.sy = AY.s;
+    q.lox = AX.lo;
+    q.loy = AY.lo;
+    q.spanx = AX.span;
+    q.spany = AY.span;
+    q.nwinx = AX.n_win;
+    q.nwiny = AY.n_win;
+    q.tiles_x = S.P.tiles_x;
+    q.tiles_y = S.P.tiles_y;
+    q.WX = S.P.WX;
+    q.WY = S.P.WY;
+    q.OX = S.P.OX;
+    q.G = S.P.G;
+    q.ICp = S.P.ICp;
+    q.IR = S.P.IR;
+    q.pad = S.P.pad;
+    q.padv = S.P.padv;
+    for (int e = 0; e < AX.r * 4; ++e) {
+        const int j = e >> 2, t = e & 3;
+        S.wx[e] = t < AX.nt_src ? AX.wf[j * AX.nt_src + t] : 0.f;
+    }
+    for (int e = 0; e < AY.r * 4; ++e) {
+        const int j = e >> 2, t = e & 3;
+        S.wy[e] = t < AY.nt_src ? AY.wf[j * AY.nt_src + t] : 0.f;
+    }
+    for (int e = 0; e < AX.r; ++e) S.offx[e] = AX.off[e];
+    for (int e = 0; e < AY.r; ++e) S.offy[e] = AY.off[e];
+}
 
 // Four adjacent outputs of one row: a 16-byte (FP32) or 8-byte (BF16) store
 // when aligned and inside the row, else element by element.
@@ -95,22 +151,37 @@ __device__ __forceinline__ void serve_tile_body(const ServeReq& q, const ServeTi
     __syncthreads();
     // ---- x pass: thread = (window ixl, row group); sH[ry][ixl rx + jx]
     const int rx = q.rx;
-    if (rx <= 8 && q.spanx <= MAXSPAN) {
+    constexpr int RW = NT == 4 ? 5 : 8;  // phases a window-per-thread x pass holds in registers
+    if (rx <= RW && q.spanx <= MAXSPAN) {
         const int nthr = g.nwx;
         const int G1 = blockDim.x / nthr;
         const int ixl = threadIdx.x % nthr, grp = threadIdx.x / nthr;
         if (grp < G1) {
-            for (int ry = grp; ry < g.rows; ry += G1) {
-                const float* row = sIn + ry * q.ICp + ixl * q.sx;
-                float* dst = sH + ry * OX + ixl * rx;
-                for (int jx = 0; jx < rx; ++jx) {
-                    const float* src = row + offx[jx];
-                    const float* w = sWx + jx * 4;
-                    float acc = 0.f;
+            // the phases' taps and offsets in registers (phases beyond rx are never used)
+            float w[RW][NT];
+            int of[RW];
 #pragma unroll
-                    for (int t = 0; t < NT; ++t) acc = fmaf(w[t], src[t], acc);
-                    dst[jx] = acc;
+            for (int jx = 0; jx < RW; ++jx) {
+                of[jx] = jx < rx ? offx[jx] : 0;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) w[jx][t] = jx < rx ? sWx[jx * 4 + t] : 0.f;
+            }
+            const float* row = sIn + grp * q.ICp + ixl * q.sx;
+            float* dst = sH + grp * OX + ixl * rx;
+            const int rstep = G1 * q.ICp, dstep = G1 * OX;
+            for (int ry = grp; ry < g.rows; ry += G1) {
+#pragma unroll
+                for (int jx = 0; jx < RW; ++jx) {
+                    if (jx < rx) {
+                        const float* src = row + of[jx];
+                        float acc = 0.f;
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) acc = fmaf(w[jx][t], src[t], acc);
+                        dst[jx] = acc;
+                    }
                 }
+                row += rstep;
+                dst += dstep;
             }
         }
     } else {
@@ -143,27 +214,38 @@ __device__ __forceinline__ void serve_tile_body(const ServeReq& q, const ServeTi
     Tout* yp = static_cast<Tout*>(q.y) + (long long)g.plane * q.Ho * q.Wo + gox;
     const bool vec = nvalid == 4 && (OX % 4) == 0 &&
                      (reinterpret_cast<uintptr_t>(yp) % (4 * sizeof(Tout))) == 0 && (q.Wo % 4) == 0;
-    const int nrow = g.nwy * q.ry;
+    const int nrow = min(g.nwy * q.ry, q.Ho - g.iy0 * q.ry);
+    // output row orow of the tile = window iyl, phase jy, walked without division
+    const int di = G2 / q.ry, dj = G2 - di * q.ry;
+    int iyl = grp / q.ry, jy = grp - iyl * q.ry;
+    const bool ox4 = (OX % 4) == 0;
+    Tout* yrow = yp + (long long)(g.iy0 * q.ry + grp) * q.Wo;
+    const long long ystep = (long long)G2 * q.Wo;
     for (int orow = grp; orow < nrow; orow += G2) {
-        const int iyl = orow / q.ry, jy = orow - iyl * q.ry;
-        const int oy = (g.iy0 + iyl) * q.ry + jy;
-        if (oy >= q.Ho) continue;
         const float* col = sH + (iyl * q.sy + offy[jy]) * OX + ox;
-        const float* wy = sWy + jy * 4;
+        const float4 wy = *reinterpret_cast<const float4*>(sWy + jy * 4);
+        const float wt[4] = {wy.x, wy.y, wy.z, wy.w};
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             float h[4];
-            if ((OX % 4) == 0) {
+            if (ox4) {
                 const float4 v = *reinterpret_cast<const float4*>(col + t * OX);
                 h[0] = v.x, h[1] = v.y, h[2] = v.z, h[3] = v.w;
             } else {
                 for (int i = 0; i < 4; ++i) h[i] = ox + i < OX ? col[t * OX + i] : 0.f;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fmaf(wy[t], h[i], acc[i]);
+            for (int i = 0; i < 4; ++i) acc[i] = fmaf(wt[t], h[i], acc[i]);
         }
-        store4(yp + (long long)oy * q.Wo, nvalid, vec, acc);
+        store4(yrow, nvalid, vec, acc);
+        yrow += ystep;
+        iyl += di;
+        jy += dj;
+        if (jy >= q.ry) {
+            jy -= q.ry;
+            ++iyl;
+        }
     }
 }
 
@@ -175,95 +257,56 @@ __device__ __forceinline__ void serve_tile(const ServeReq& q, const ServeTile& g
     else serve_tile_body<4, Tin, Tout>(q, g, sWx, sWy, offx, offy, sIn);
 }
 
-// K6: a persistent grouped kernel.  CTA b takes the work items [b per, (b+1) per)
-// in order (the items of one request are consecutive, so the request's
-// parameters are staged once per run of its tiles); each item names a request
-// slot and one of its tiles.
+// K6: a persistent grouped kernel.  The CTAs take chunks of consecutive work
+// items round-robin (the items of one request are consecutive, so a request's
+// record is staged once per run of its tiles); each item names a request slot
+// and one of its tiles.
 template <typename Tout>
 __global__ void __launch_bounds__(kServeThreads) fcfs_serve_grouped(const ServeSlot* __restrict__ slots,
-                                                                     const WorkItem* __restrict__ work, int n_items) {
+                                                                     const WorkItem* __restrict__ work, int n_items,
+                                                                     int chunk) {
     extern __shared__ __align__(16) float smem[];
     __shared__ ServeReq sq;
-    __shared__ ServeTile st;
-    __shared__ float sWx[kMaxR * 4], sWy[kMaxR * 4];
+    __shared__ __align__(16) float sWx[kMaxR * 4];
+    __shared__ __align__(16) float sWy[kMaxR * 4];
     __shared__ short offx[kMaxR], offy[kMaxR];
-    const int per = (n_items + gridDim.x - 1) / gridDim.x;
-    const int k0 = blockIdx.x * per, k1 = min(n_items, k0 + per);
+    const TileDeal deal = deal_tiles(n_items, chunk);
     int last_slot = -1;
-    for (int k = k0; k < k1; ++k) {
-        const WorkItem w = work[k];
+    for (int kk = 0; kk < deal.n; ++kk) {
+        const WorkItem w = work[deal.tile(kk)];
         __syncthreads();  // the previous tile is done with the staged parameters and buffers
         if (w.slot != last_slot) {
+            // the slot's compact record, copied by all threads
             const ServeSlot& S = slots[w.slot];
-            const AxisP& AX = S.P.ax[2];
-            const AxisP& AY = S.P.ax[1];
-            for (int e = threadIdx.x; e < AX.r * 4; e += blockDim.x) {
-                const int j = e >> 2, t = e & 3;
-                sWx[e] = t < AX.nt_src ? AX.wf[j * AX.nt_src + t] : 0.f;
-            }
-            for (int e = threadIdx.x; e < AY.r * 4; e += blockDim.x) {
-                const int j = e >> 2, t = e & 3;
-                sWy[e] = t < AY.nt_src ? AY.wf[j * AY.nt_src + t] : 0.f;
-            }
-            for (int e = threadIdx.x; e < AX.r; e += blockDim.x) offx[e] = AX.off[e];
-            for (int e = threadIdx.x; e < AY.r; e += blockDim.x) offy[e] = AY.off[e];
-            if (threadIdx.x == 0) {
-                ServeReq q;
-                q.x = S.P.x;
-                q.y = S.P.y;
-                q.din = S.din;
-                q.nt = S.nt;
-                q.H = AY.n_in;
-                q.W = AX.n_in;
-                q.Ho = AY.n_out;
-                q.Wo = AX.n_out;
-                q.rx = AX.r;
-                q.sx = AX.s;
-                q.ry = AY.r;
-                q.sy = AY.s;
-                q.lox = AX.lo;
-                q.loy = AY.lo;
-                q.spanx = AX.span;
-                q.spany = AY.span;
-                q.nwinx = AX.n_win;
-                q.nwiny = AY.n_win;
-                q.tiles_x = S.P.tiles_x;
-                q.tiles_y = S.P.tiles_y;
-                q.WX = S.P.WX;
-                q.WY = S.P.WY;
-                q.OX = S.P.OX;
-                q.G = S.P.G;
-                q.ICp = S.P.ICp;
-                q.IR = S.P.IR;
-                q.pad = S.P.pad;
-                q.padv = S.P.padv;
-                sq = q;
-            }
+            const int rx = S.q.rx, ry = S.q.ry;
+            static_assert(sizeof(ServeReq) % 4 == 0, "record copied in 4-byte words");
+            const int* qsrc = reinterpret_cast<const int*>(&S.q);
+            int* qdst = reinterpret_cast<int*>(&sq);
+            for (int e = threadIdx.x; e < (int)(sizeof(ServeReq) / 4); e += blockDim.x) qdst[e] = qsrc[e];
+            for (int e = threadIdx.x; e < rx * 4; e += blockDim.x) sWx[e] = S.wx[e];
+            for (int e = threadIdx.x; e < ry * 4; e += blockDim.x) sWy[e] = S.wy[e];
+            for (int e = threadIdx.x; e < rx; e += blockDim.x) offx[e] = S.offx[e];
+            for (int e = threadIdx.x; e < ry; e += blockDim.x) offy[e] = S.offy[e];
             last_slot = w.slot;
+            __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            // tile index -> geometry in 32-bit arithmetic (a request has fewer than 2^31 tiles)
-            const ServeSlot& S = slots[w.slot];
-            const int txy = S.P.tiles_x * S.P.tiles_y;
-            ServeTile g;
+        const ServeReq q = sq;
+        // tile index -> geometry in 32-bit arithmetic (a request has fewer than 2^31 tiles)
+        ServeTile g;
+        {
+            const int txy = q.tiles_x * q.tiles_y;
             g.plane = w.tile / txy;
             const int rem = w.tile - g.plane * txy;
-            const int ty = rem / S.P.tiles_x, tx = rem - ty * S.P.tiles_x;
-            const AxisP& AX = S.P.ax[2];
-            const AxisP& AY = S.P.ax[1];
-            g.ix0 = tx * S.P.WX;
-            g.iy0 = ty * S.P.WY;
-            g.nwx = min(S.P.WX, AX.n_win - g.ix0);
-            g.nwy = min(S.P.WY, AY.n_win - g.iy0);
-            g.cols = (g.nwx - 1) * AX.s + AX.span;
-            g.rows = (g.nwy - 1) * AY.s + AY.span;
-            g.col0 = g.ix0 * AX.s + AX.lo;
-            g.row0 = g.iy0 * AY.s + AY.lo;
-            st = g;
+            const int ty = rem / q.tiles_x, tx = rem - ty * q.tiles_x;
+            g.ix0 = tx * q.WX;
+            g.iy0 = ty * q.WY;
+            g.nwx = min(q.WX, q.nwinx - g.ix0);
+            g.nwy = min(q.WY, q.nwiny - g.iy0);
+            g.cols = (g.nwx - 1) * q.sx + q.spanx;
+            g.rows = (g.nwy - 1) * q.sy + q.spany;
+            g.col0 = g.ix0 * q.sx + q.lox;
+            g.row0 = g.iy0 * q.sy + q.loy;
         }
-        __syncthreads();
-        const ServeReq q = sq;
-        const ServeTile g = st;
         if (q.din == FCFS_U8) serve_tile<uint8_t, Tout>(q, g, sWx, sWy, offx, offy, smem);
         else if (q.din == FCFS_F32) serve_tile<float, Tout>(q, g, sWx, sWy, offx, offy, smem);
         else serve_tile<__nv_bfloat16, Tout>(q, g, sWx, sWy, offx, offy, smem);
@@ -322,9 +365,9 @@ int launch_step(Server& sv, StepRec& R) {
     if (e != cudaSuccess) return cuda_fail(e, "serve work list copy");
     const unsigned grid = (unsigned)std::min<long long>(n, (long long)sv.grid_cap);
     if (sv.cfg.out_dtype == FCFS_BF16)
-        fcfs_serve_grouped<__nv_bfloat16><<<grid, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev, (int)n);
+        fcfs_serve_grouped<__nv_bfloat16><<<grid, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev, (int)n, kServeChunk);
     else
-        fcfs_serve_grouped<float><<<grid, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev, (int)n);
+        fcfs_serve_grouped<float><<<grid, kServeThreads, kServeMaxSmem, sv.stream>>>(sv.slots_dev, R.dev, (int)n, kServeChunk);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "serve grouped launch");
     e = cudaEventRecord(R.ev, sv.stream);
@@ -380,6 +423,7 @@ void worker_loop(Server* sv) {
                 // with auto_release the block is reused once the request completes
                 if (!sv->cfg.auto_release) sv->out_of[r->id] = {sl.P.y, sv->cfg.out_dtype};
             }
+            fill_serve_rec(sl);
             smin = std::min(smin, r->slot);
             smax = std::max(smax, r->slot);
             progressed = true;
