@@ -26,7 +26,9 @@ namespace fcfs {
 namespace {
 
 constexpr int kServeThreads = 256;
-constexpr int kServeMaxSmem = 48 * 1024;  // four CTAs per SM (the register limit too)
+// four CTAs per SM (the register limit too); larger budgets (taller tiles, fewer CTAs) measured
+// slower: 72 KB 91, 96 KB 72, 144 KB 43 Gpix/s against 98 on the mixed stream
+constexpr int kServeMaxSmem = 48 * 1024;
 // work items dealt to the CTAs in chunks of four consecutive items (tiles of one request,
 // mostly): tile costs differ across requests, and contiguous runs left SMs idle at the end
 // of a step (75 -> 97 Gpix/s on the mixed stream)
