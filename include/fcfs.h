@@ -192,9 +192,40 @@ typedef struct {
  * w2d must be NULL; r_y r_x <= 512); x: DEVICE [n][c][H][W] of dtype_in;
  * y: DEVICE [n][c_out][Ho][Wo] of dtype_out, fully overwritten.  FP32
  * arithmetic.  Errors: as fcfs_forward, FCFS_ERR_ARG for a bad epilogue,
- * FCFS_ERR_UNSUPPORTED outside the 2D separable layer.  Forward only.
+ * FCFS_ERR_UNSUPPORTED outside the 2D separable layer.  Gradients:
+ * fcfs_backward_fused.
  */
 int fcfs_forward_fused(const fcfs_desc* d, const fcfs_epilogue* e, const void* x, void* y, void* stream);
+
+/*
+ * Bytes of DEVICE workspace fcfs_backward_fused needs for descriptor d and
+ * epilogue e (the recomputed FCFS outputs, the pre-activation gradient, the
+ * partial sums of the mix gradient, and fcfs_backward's own workspace); 0 when
+ * d or e is invalid (fcfs_last_error says why).
+ */
+size_t fcfs_backward_fused_workspace(const fcfs_desc* d, const fcfs_epilogue* e);
+
+/*
+ * Gradients of the fused layer (Sec. 1: the resize trained as one layer of
+ * an FCN; the layer of fcfs_forward_fused).  With z = FCFS(x) and
+ * v = mix z + bias recomputed in FP32 and gv = gy act'(v):
+ *   gmix[o][c] = sum_{n,p} gv[n,o,p] z[n,c,p]   gbias[o] = sum_{n,p} gv[n,o,p]
+ *   gz[n,c,p]  = sum_o mix[o][c] gv[n,o,p]      (gz = gv without a mix)
+ * and gx, gw are the FCFS gradients for the upstream gradient gz (as
+ * fcfs_backward).  act': relu 1 for v > 0 else 0; leaky relu 1 for v > 0
+ * else alpha; clamp 1 for lo <= v <= hi else 0; none 1.
+ * d, e: as for the forward (dtype_out is gy's type, FP32 or BF16; dtype_in
+ * FP32 or BF16).  x: DEVICE input; gy: DEVICE [n][c_out][Ho][Wo]; gx: DEVICE
+ * like x or NULL; gmix: DEVICE FP32 [c_out][c] or NULL (needs a mix); gbias:
+ * DEVICE FP32 [c_out] or NULL (needs a bias); gw: as for fcfs_backward (or
+ * NULL).  Every requested output is overwritten.  workspace: DEVICE, 256-byte
+ * aligned, at least fcfs_backward_fused_workspace(d, e) bytes.  Results are
+ * reproducible bit for bit (fixed summation orders).  Errors: as
+ * fcfs_backward; FCFS_ERR_ARG for a bad epilogue, a missing or small
+ * workspace, or a gradient of a term the layer does not have.
+ */
+int fcfs_backward_fused(const fcfs_desc* d, const fcfs_epilogue* e, const void* x, const void* gy, void* gx,
+                        float* gmix, float* gbias, float* const* gw, void* workspace, size_t ws_bytes, void* stream);
 
 /*
  * Bytes of device workspace fcfs_backward needs for the weight gradients

@@ -324,7 +324,9 @@ def resize_fused(x, axes, mix=None, bias=None, act=ACT_NONE, alpha=0.0, lo=0.0, 
     Float64 throughout; the channel sum is a library matrix product (one step)."""
     if align is not None:
         axes = [dict(a, align=align) for a in axes]
-    z = resize(x, axes, pad=pad, pad_value=pad_value)
+    # learnable taps: the strided-convolution sum with the learned weights (Sec. 3.1); fixed
+    # methods: the direct interpolation formula
+    z = resize(x, axes, pad=pad, pad_value=pad_value, polyphase=any(a.get("w") is not None for a in axes))
     nd = z.ndim - 2
     if mix is None:
         v = z.copy()
@@ -342,3 +344,55 @@ def resize_fused(x, axes, mix=None, bias=None, act=ACT_NONE, alpha=0.0, lo=0.0, 
     elif act != ACT_NONE:
         raise ValueError("unknown activation")
     return v
+
+
+def act_derivative(v, act, alpha=0.0, lo=0.0, hi=0.0):
+    """Derivative of the fused layer's activation at the pre-activation v, with the
+    conventions of the common frameworks at the kinks: relu 1 for v > 0 else 0; leaky relu
+    1 for v > 0 else alpha; clamp 1 for lo <= v <= hi else 0; none 1."""
+    v = np.asarray(v, dtype=np.float64)
+    if act == ACT_NONE:
+        return np.ones_like(v)
+    if act == ACT_RELU:
+        return (v > 0.0).astype(np.float64)
+    if act == ACT_LEAKY_RELU:
+        return np.where(v > 0.0, 1.0, alpha)
+    if act == ACT_CLAMP:
+        return ((v >= lo) & (v <= hi)).astype(np.float64)
+    raise ValueError("unknown activation")
+
+
+def resize_fused_backward(x, gy, axes, mix=None, bias=None, act=ACT_NONE, alpha=0.0, lo=0.0, hi=0.0,
+                          pad=PAD_REPLICATE, pad_value=0.0, align=None):
+    """Gradients of the fused layer y = act(mix z + bias), z = FCFS(x), for the upstream
+    gradient gy, by the chain rule step by step (float64):
+        v = mix z + bias,  gv = gy act'(v),
+        gmix[o][c] = sum_{n,p} gv[n,o,p] z[n,c,p],  gbias[o] = sum_{n,p} gv[n,o,p],
+        gz = mix^T gv (gz = gv without a mix),
+        gx = the FCFS input gradient of gz, gw = the FCFS weight gradients of gz.
+    Returns (gx, gmix, gbias, gw list); gmix / gbias None where the layer has no such term."""
+    if align is not None:
+        axes = [dict(a, align=align) for a in axes]
+    x = np.asarray(x, dtype=np.float64)
+    gy = np.asarray(gy, dtype=np.float64)
+    z = resize(x, axes, pad=pad, pad_value=pad_value, polyphase=any(a.get("w") is not None for a in axes))
+    nd = z.ndim - 2
+    if mix is None:
+        v = z.copy()
+    else:
+        mix = np.asarray(mix, dtype=np.float64)
+        v = np.einsum("oc,nc...->no...", mix, z)
+    if bias is not None:
+        v = v + np.asarray(bias, dtype=np.float64).reshape((1, -1) + (1,) * nd)
+    gv = gy * act_derivative(v, act, alpha, lo, hi)
+    axes_sum = (0,) + tuple(range(2, 2 + nd))
+    gbias = gv.sum(axis=axes_sum) if bias is not None else None
+    if mix is None:
+        gmix, gz = None, gv
+    else:
+        gmix = np.einsum("nop,ncp->oc", gv.reshape(gv.shape[0], gv.shape[1], -1), z.reshape(z.shape[0], z.shape[1], -1))
+        gz = np.einsum("oc,no...->nc...", mix, gv)
+    gx = adjoint_dx(gz, x.shape[2:], axes, pad=pad)
+    learn = [a for a in axes if a.get("w") is not None]
+    gw = weight_grad(x, gz, axes, pad=pad, pad_value=pad_value) if learn else [None] * len(axes)
+    return gx, gmix, gbias, gw

@@ -77,6 +77,9 @@ SIGNATURES = {
     "fcfs_forward": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P]),
     "fcfs_forward_fused": (_I, [ctypes.POINTER(fcfs_desc), ctypes.POINTER(fcfs_epilogue), _P, _P, _P]),
     "fcfs_backward_workspace": (ctypes.c_size_t, [ctypes.POINTER(fcfs_desc)]),
+    "fcfs_backward_fused_workspace": (ctypes.c_size_t, [ctypes.POINTER(fcfs_desc), ctypes.POINTER(fcfs_epilogue)]),
+    "fcfs_backward_fused": (_I, [ctypes.POINTER(fcfs_desc), ctypes.POINTER(fcfs_epilogue), _P, _P, _P, _P, _P, _P, _P,
+                                 ctypes.c_size_t, _P]),
     "fcfs_backward": (_I, [ctypes.POINTER(fcfs_desc), _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "fcfs_status_string": (ctypes.c_char_p, [_I]),
     "fcfs_last_error": (ctypes.c_char_p, []),

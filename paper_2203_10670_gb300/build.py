@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfcfs.so")
-SOURCES = ["fcfs_host.cu", "fcfs_fwd.cu", "fcfs_fwd_tma.cu", "fcfs_fwd_tma_f32.cu", "fcfs_fwd_tma_bf16.cu", "fcfs_fwd_tma_u8.cu", "fcfs_fwd_rs_f32.cu", "fcfs_fwd_rs_bf16.cu", "fcfs_fwd3d_tma.cu", "fcfs_fwd3d_rs.cu", "fcfs_bwd.cu", "fcfs_bwd_tma.cu", "fcfs_bwd_dx_rs.cu", "fcfs_bwd_dx3d_tma.cu", "fcfs_full2d.cu", "fcfs_fused.cu", "fcfs_fused_tc.cu", "fcfs_tune.cu", "fcfs_serve.cu", "fcfs_noalloc.cu", "fcfs_psk_f32.cu", "fcfs_psk_bf16.cu", "fcfs_psk_host.cu"]
+SOURCES = ["fcfs_host.cu", "fcfs_fwd.cu", "fcfs_fwd_tma.cu", "fcfs_fwd_tma_f32.cu", "fcfs_fwd_tma_bf16.cu", "fcfs_fwd_tma_u8.cu", "fcfs_fwd_rs_f32.cu", "fcfs_fwd_rs_bf16.cu", "fcfs_fwd3d_tma.cu", "fcfs_fwd3d_rs.cu", "fcfs_bwd.cu", "fcfs_bwd_tma.cu", "fcfs_bwd_dx_rs.cu", "fcfs_bwd_dx3d_tma.cu", "fcfs_full2d.cu", "fcfs_fused.cu", "fcfs_fused_tc.cu", "fcfs_fused_bwd.cu", "fcfs_tune.cu", "fcfs_serve.cu", "fcfs_noalloc.cu", "fcfs_psk_f32.cu", "fcfs_psk_bf16.cu", "fcfs_psk_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -321,6 +321,67 @@ def fcfs_forward_fused(desc: N.fcfs_desc, epi: N.fcfs_epilogue, x_ptr: int, y_pt
           "fcfs_forward_fused")
 
 
+def fcfs_backward_fused_workspace(desc: N.fcfs_desc, epi: N.fcfs_epilogue) -> int:
+    return int(N.load().fcfs_backward_fused_workspace(ctypes.byref(desc), ctypes.byref(epi)))
+
+
+def fcfs_backward_fused(desc, epi, x_ptr, gy_ptr, gx_ptr, gmix_ptr, gbias_ptr, gw_ptrs, ws_ptr, ws_bytes,
+                        stream=0) -> None:
+    arr = None
+    if gw_ptrs is not None:
+        arr = (ctypes.c_void_p * 3)(*(list(gw_ptrs) + [None] * (3 - len(gw_ptrs))))
+    check(N.load().fcfs_backward_fused(ctypes.byref(desc), ctypes.byref(epi), x_ptr, gy_ptr, gx_ptr, gmix_ptr,
+                                       gbias_ptr, ctypes.cast(arr, ctypes.c_void_p) if arr is not None else None,
+                                       ws_ptr, ws_bytes, stream), "fcfs_backward_fused")
+
+
+def _fused_epilogue(c: int, mix, bias, act, alpha, lo, hi) -> N.fcfs_epilogue:
+    e = N.fcfs_epilogue()
+    for name, t in (("mix", mix), ("bias", bias)):
+        if t is not None and (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    e.c_out = int(mix.shape[0]) if mix is not None else int(c)
+    if mix is not None and tuple(mix.shape) != (e.c_out, c):
+        raise ValueError("mix must be [c_out, c]")
+    if bias is not None and tuple(bias.shape) != (e.c_out,):
+        raise ValueError("bias must be [c_out]")
+    e.mix = mix.data_ptr() if mix is not None else None
+    e.bias = bias.data_ptr() if bias is not None else None
+    e.act, e.alpha, e.lo, e.hi = int(act), float(alpha), float(lo), float(hi)
+    return e
+
+
+def resize_fused_backward(x: torch.Tensor, gy: torch.Tensor, axes: Sequence[Axis], mix: Optional[torch.Tensor] = None,
+                          bias: Optional[torch.Tensor] = None, act: int = ACT_NONE, alpha: float = 0.0,
+                          lo: float = 0.0, hi: float = 0.0, pad: int = PAD_REPLICATE, pad_value: float = 0.0,
+                          align: int = ALIGN_PAPER, cubic_a: float = 0.0, need_dx: bool = True,
+                          need_dmix: bool = False, need_dbias: bool = False, need_dw: Sequence[bool] = ()):
+    """(gx, gmix, gbias, [gw per axis]) of y = act(mix @ FCFS(x) + bias) for the upstream gradient gy
+    (fcfs_backward_fused); entries not asked for are None."""
+    x = x.contiguous()
+    gy = gy.contiguous()
+    d = make_desc(x.shape, axes, _DT[x.dtype], _DT[gy.dtype], pad, pad_value, align, cubic_a)
+    e = _fused_epilogue(x.shape[1], mix, bias, act, alpha, lo, hi)
+    dev = x.device
+    gx = torch.empty_like(x) if need_dx else None
+    gmix = torch.empty_like(mix) if need_dmix and mix is not None else None
+    gbias = torch.empty_like(bias) if need_dbias and bias is not None else None
+    gws, ptrs = [], []
+    for a, ax in enumerate(axes):
+        want = bool(need_dw[a]) if a < len(need_dw) else False
+        g = torch.empty_like(ax.w) if want and ax.w is not None else None
+        gws.append(g)
+        ptrs.append(g.data_ptr() if g is not None else None)
+    ws_bytes = fcfs_backward_fused_workspace(d, e)
+    if ws_bytes == 0:  # the descriptor or epilogue was refused (the library's message says why)
+        raise N.FCFSError(N.FCFS_ERR_ARG, "fcfs_backward_fused_workspace")
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    fcfs_backward_fused(d, e, x.data_ptr(), gy.data_ptr(), gx.data_ptr() if gx is not None else None,
+                        gmix.data_ptr() if gmix is not None else None, gbias.data_ptr() if gbias is not None else None,
+                        ptrs, ws.data_ptr(), ws_bytes, _stream(dev))
+    return gx, gmix, gbias, gws
+
+
 def resize_fused(x: torch.Tensor, axes: Sequence[Axis], mix: Optional[torch.Tensor] = None,
                  bias: Optional[torch.Tensor] = None, act: int = ACT_NONE, alpha: float = 0.0, lo: float = 0.0,
                  hi: float = 0.0, pad: int = PAD_REPLICATE, pad_value: float = 0.0,
@@ -333,18 +394,7 @@ def resize_fused(x: torch.Tensor, axes: Sequence[Axis], mix: Optional[torch.Tens
         out_dtype = out.dtype if out is not None else torch.float32 if x.dtype == torch.uint8 else x.dtype
     x = x.contiguous()
     d = make_desc(x.shape, axes, _DT[x.dtype], _DT[out_dtype], pad, pad_value, align, cubic_a, antialias)
-    e = N.fcfs_epilogue()
-    for name, t in (("mix", mix), ("bias", bias)):
-        if t is not None and (t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous()):
-            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
-    e.c_out = int(mix.shape[0]) if mix is not None else int(x.shape[1])
-    if mix is not None and tuple(mix.shape) != (e.c_out, x.shape[1]):
-        raise ValueError("mix must be [c_out, c]")
-    if bias is not None and tuple(bias.shape) != (e.c_out,):
-        raise ValueError("bias must be [c_out]")
-    e.mix = mix.data_ptr() if mix is not None else None
-    e.bias = bias.data_ptr() if bias is not None else None
-    e.act, e.alpha, e.lo, e.hi = int(act), float(alpha), float(lo), float(hi)
+    e = _fused_epilogue(x.shape[1], mix, bias, act, alpha, lo, hi)
     oshape = (x.shape[0], e.c_out) + out_shape(x.shape, axes)[2:]
     if out is None:
         out = torch.empty(oshape, dtype=out_dtype, device=x.device)
