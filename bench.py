@@ -669,7 +669,26 @@ def fused_times(fcfs, inputs, device, stream, peak, batch=None, steps=5, warmup=
     flop = 2.0 * 64 * 64 * px + 2.0 * 2 * 2 * x.shape[1] * px  # mix, plus two 2-tap passes per channel
     out = {"ms": tf * 1e3, "Gpix_s": px / tf / 1e9, "hbm_frac": nbytes / tf / 1e9 / peak,
            "alu_frac": flop / tf / 1e12 / FP32_ALU_TFLOPS, "unfused_ms": tu * 1e3}
-    del x, y, z
+    # the layer's backward (input, mix and bias gradients): fcfs_backward_fused against torch's
+    # 1x1 convolution and ReLU backward followed by the plain FCFS input gradient
+    gy = inputs.normal(tuple(y.shape), 84, device=device, dtype=dtype)
+
+    def fused_bwd():
+        fcfs.resize_fused_backward(x, gy, ax, mix, b, fcfs.ACT_RELU, need_dmix=True, need_dbias=True)
+
+    wq = w4.detach().clone().requires_grad_(True)
+    bq = bd.detach().clone().requires_grad_(True)
+
+    def unfused_bwd():
+        zq = fcfs.resize(x, ax).requires_grad_(True)
+        v = torch.relu(torch.nn.functional.conv2d(zq, wq, bq))
+        gz, _, _ = torch.autograd.grad(v, (zq, wq, bq), gy)
+        fcfs.resize_backward(None, gz, ax, in_shape=tuple(x.shape), in_dtype=x.dtype)
+
+    fused_bwd(), unfused_bwd()
+    out["bwd_ms"] = timed(fused_bwd, steps, stream) / steps * 1e3
+    out["bwd_unfused_ms"] = timed(unfused_bwd, steps, stream) / steps * 1e3
+    del x, y, z, gy
     # the epilogue alone: the c2 images (16x3x1080x1920), bicubic 4/3, clamped to [0, 1] on store,
     # against the plain resize followed by an in-place clamp (one more pass over the output)
     xs = inputs.uniform(inputs.C2["shape"], inputs.C2["seed"], device=device, dtype=dtype)

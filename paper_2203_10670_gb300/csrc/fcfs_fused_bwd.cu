@@ -54,30 +54,40 @@ __device__ __forceinline__ float load_gy(const ActP& a, long long i) {
 // order, written at C[b scb + m scm + n].  EPI_GRAD: C = gy(b, m, n)
 // act'(C + bias[m]), C and gy dense [b][M][N].  The batch b = blockIdx.z is an
 // image, or one pixel range of a split product.
+// Split products (S > 1): batch z = image z / S, pixel range z % S of kr
+// pixels each (the last one shorter, K the full length), the range's offset
+// applied along each operand's k stride.
 template <int EPI>
 __global__ void __launch_bounds__(256) fused_mm(int M, int N, int K, View A, View B, float* C, long long scb,
-                                                long long scm, ActP act) {
+                                                long long scm, ActP act, int S, int kr) {
     __shared__ float As[kBK][kBM + 4];
     __shared__ float Bs[kBK][kBN + 4];
     const int b = blockIdx.z;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const float* Ap = A.p + b * A.sb;
-    const float* Bp = B.p + b * B.sb;
+    const int img = b / S, sp = b - img * S;
+    const long long k_off = (long long)sp * kr;
+    if (S > 1) K = (int)min((long long)kr, (long long)K - k_off);
+    const float* Ap = A.p + img * A.sb + k_off * A.sj;
+    const float* Bp = B.p + img * B.sb + k_off * B.si;
+    const bool a_k_unit = A.sj == 1, b_n_unit = B.sj == 1;
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     for (int k0 = 0; k0 < K; k0 += kBK) {
-        // 64 x 16 elements of each operand, four per thread
+        // 64 x 16 elements of each operand, four per thread; consecutive threads take the
+        // operand's unit-stride index, so the loads coalesce whichever index it is
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = threadIdx.x + q * 256;
-            const int kk = e & (kBK - 1), mm = e >> 4;
+            const int kk = a_k_unit ? (e & (kBK - 1)) : (e >> 6);
+            const int mm = a_k_unit ? (e >> 4) : (e & (kBM - 1));
             const int gm = m0 + mm, gk = k0 + kk;
             As[kk][mm] = (gm < M && gk < K) ? Ap[gm * A.si + gk * A.sj] : 0.f;
-            const int nn = e & (kBN - 1), kb = e >> 6;
+            const int nn = b_n_unit ? (e & (kBN - 1)) : (e >> 4);
+            const int kb = b_n_unit ? (e >> 6) : (e & (kBK - 1));
             const int gn = n0 + nn, gk2 = k0 + kb;
             Bs[kb][nn] = (gn < N && gk2 < K) ? Bp[gk2 * B.si + gn * B.sj] : 0.f;
         }
@@ -134,14 +144,17 @@ __global__ void fused_sum_rows(const float* in, int nb, int len, float* out) {
     out[o] = s;
 }
 
-// gb[o] = sum_{n,p} gv[n,o,p]: one block per o, fixed-order partial sums and tree
-__global__ void __launch_bounds__(256) fused_bias_grad(const float* gv, int n, int O, long long P, float* gb) {
+// part[s][o] = sum over the images and pixel range s (of kr pixels) of gv[n,o,p]: block (o, s),
+// fixed-order partial sums and tree; fused_sum_rows then adds the ranges in order
+__global__ void __launch_bounds__(256) fused_bias_grad(const float* gv, int n, int O, long long P, long long kr,
+                                                       float* part) {
     __shared__ float red[256];
-    const int o = blockIdx.x;
+    const int o = blockIdx.x, sp = blockIdx.y;
+    const long long p0 = sp * kr, p1 = min(P, p0 + kr);
     float s = 0.f;
     for (int b = 0; b < n; ++b) {
         const float* row = gv + ((long long)b * O + o) * P;
-        for (long long p = threadIdx.x; p < P; p += blockDim.x) s += row[p];
+        for (long long p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += row[p];
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -149,7 +162,7 @@ __global__ void __launch_bounds__(256) fused_bias_grad(const float* gv, int n, i
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gb[o] = red[0];
+    if (threadIdx.x == 0) part[(long long)sp * O + o] = red[0];
 }
 
 struct FusedBwdLayout {
@@ -169,7 +182,8 @@ int fused_bwd_layout(const fcfs_desc* d, const fcfs_epilogue* e, FusedBwdLayout*
     L->part_off = L->gv_off + al((size_t)(n * O * P) * 4);
     L->splits = (int)std::max<long long>(1, std::min<long long>((304 + n - 1) / n, (P + 4095) / 4096));
     L->krange = (P + L->splits - 1) / L->splits;
-    L->ws_off = L->part_off + al((size_t)(n * L->splits) * O * C * 4);
+    // partial sums of the mix gradient, then (reused) of the bias gradient: at most 64 ranges
+    L->ws_off = L->part_off + al((size_t)std::max<long long>(n * L->splits * O * C, 64 * O) * 4);
     L->total = L->ws_off + al(fcfs_backward_workspace(&dz));
     return FCFS_OK;
 }
@@ -249,7 +263,7 @@ extern "C" int fcfs_backward_fused(const fcfs_desc* d, const fcfs_epilogue* e, c
         View A{e->mix, 0, C, 1};          // M[o][c]
         View B{z, (long long)C * P, P, 1};  // z[n][c][p]
         dim3 grid((unsigned)((P + kBN - 1) / kBN), (unsigned)((O + kBM - 1) / kBM), (unsigned)n);
-        fused_mm<EPI_GRAD><<<grid, 256, 0, st>>>(O, (int)P, C, A, B, gv, (long long)O * P, P, ap);
+        fused_mm<EPI_GRAD><<<grid, 256, 0, st>>>(O, (int)P, C, A, B, gv, (long long)O * P, P, ap, 1, C);
     } else {
         const long long total = (long long)n * C * P;
         fused_grad_identity<<<(unsigned)std::min<long long>((total + 255) / 256, 152LL * 16), 256, 0, st>>>(total, C, P, z, gv, ap);
@@ -258,32 +272,22 @@ extern "C" int fcfs_backward_fused(const fcfs_desc* d, const fcfs_epilogue* e, c
     if (ce != cudaSuccess) return cuda_fail(ce, "fused backward: activation gradient");
     // gM = sum over images and pixel ranges of gv z^T (fixed-order sum of the split products)
     if (gmix) {
+        // all images' pixel ranges in one launch: part[img S + s][o][c]
         const int S = L.splits;
-        for (int b = 0; b < n; ++b) {
-            // split s of image b: pixels [s kr, (s + 1) kr), batch index = split
-            const long long kr = L.krange;
-            View A{gv + (long long)b * O * P, kr, P, 1};  // (split, o, k) -> gv[b][o][s kr + k]
-            View B{z + (long long)b * C * P, kr, 1, P};   // (split, k, c) -> z[b][c][s kr + k]
-            const int K = (int)std::min<long long>(kr, P);
-            // the last split may run past P: its view is clipped by K per split below
-            dim3 grid((unsigned)((C + kBN - 1) / kBN), (unsigned)((O + kBM - 1) / kBM), (unsigned)(S - 1));
-            if (S > 1)
-                fused_mm<EPI_STORE><<<grid, 256, 0, st>>>(O, C, K, A, B, part + (long long)b * S * O * C,
-                                                          (long long)O * C, C, ap);
-            // the last (possibly short) split
-            const long long last0 = (long long)(S - 1) * kr;
-            View Al{gv + (long long)b * O * P + last0, 0, P, 1};
-            View Bl{z + (long long)b * C * P + last0, 0, 1, P};
-            dim3 g1((unsigned)((C + kBN - 1) / kBN), (unsigned)((O + kBM - 1) / kBM), 1);
-            fused_mm<EPI_STORE><<<g1, 256, 0, st>>>(O, C, (int)(P - last0), Al, Bl,
-                                                    part + ((long long)b * S + S - 1) * O * C, 0, C, ap);
-        }
+        View A{gv, (long long)O * P, P, 1};  // (img, o, k) -> gv[img][o][k]
+        View B{z, (long long)C * P, 1, P};   // (img, k, c) -> z[img][c][k]
+        dim3 grid((unsigned)((C + kBN - 1) / kBN), (unsigned)((O + kBM - 1) / kBM), (unsigned)(n * S));
+        fused_mm<EPI_STORE><<<grid, 256, 0, st>>>(O, C, (int)P, A, B, part, (long long)O * C, C, ap, S, (int)L.krange);
         fused_sum_rows<<<(O * C + 255) / 256, 256, 0, st>>>(part, n * S, O * C, gmix);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "fused backward: mix gradient");
     }
     if (gbias) {
-        fused_bias_grad<<<O, 256, 0, st>>>(gv, n, O, P, gbias);
+        // the mix gradient's partials are summed: their space holds the bias partials now
+        const int SB = (int)std::min<long long>(64, (P + 4095) / 4096);
+        const long long krb = (P + SB - 1) / SB;
+        fused_bias_grad<<<dim3(O, SB), 256, 0, st>>>(gv, n, O, P, krb, part);
+        fused_sum_rows<<<(O + 255) / 256, 256, 0, st>>>(part, SB, O, gbias);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "fused backward: bias gradient");
     }
@@ -294,8 +298,7 @@ extern "C" int fcfs_backward_fused(const fcfs_desc* d, const fcfs_epilogue* e, c
         View A{e->mix, 0, 1, C};            // (c, o) -> M[o][c]
         View B{gv, (long long)O * P, P, 1};  // gv[n][o][p]
         dim3 grid((unsigned)((P + kBN - 1) / kBN), (unsigned)((C + kBM - 1) / kBM), (unsigned)n);
-        fused_mm<EPI_STORE><<<grid, 256, 0, st>>>(C, (int)P, O, A, B, z,
-                                                  (long long)C * P, P, ap);
+        fused_mm<EPI_STORE><<<grid, 256, 0, st>>>(C, (int)P, O, A, B, z, (long long)C * P, P, ap, 1, O);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "fused backward: channel gradient");
         gz = z;

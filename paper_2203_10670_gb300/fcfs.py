@@ -11,6 +11,7 @@ the layer runs in the CUDA kernels of libfcfs; nothing here computes.
 from __future__ import annotations
 
 import ctypes
+import math
 from dataclasses import dataclass
 from typing import Optional, Sequence
 
@@ -402,6 +403,66 @@ def resize_fused(x: torch.Tensor, axes: Sequence[Axis], mix: Optional[torch.Tens
         raise ValueError("out has the wrong shape, dtype or layout")
     fcfs_forward_fused(d, e, x.data_ptr(), out.data_ptr(), _stream(x.device))
     return out
+
+
+class FusedFunction(torch.autograd.Function):
+    """Differentiable fused layer y = act(mix @ FCFS(x) + bias): fcfs_forward_fused and
+    fcfs_backward_fused (gradients of x, mix, bias and the learnable taps)."""
+
+    @staticmethod
+    def forward(ctx, x, spec, mix, bias, *weights):
+        axes = [Axis(a.r, a.s, a.method, a.K, w) for a, w in zip(spec["axes"], weights)]
+        y = resize_fused(x, axes, mix, bias, spec["act"], spec["alpha"], spec["lo"], spec["hi"], spec["pad"],
+                         spec["pad_value"], out_dtype=spec.get("out_dtype"))
+        ctx.spec = spec
+        ctx.has = [mix is not None, bias is not None] + [w is not None for w in weights]
+        ctx.save_for_backward(x, *[t if t is not None else torch.empty(0) for t in (mix, bias, *weights)])
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, mix, bias, *ws = ctx.saved_tensors
+        spec = ctx.spec
+        mix = mix if ctx.has[0] else None
+        bias = bias if ctx.has[1] else None
+        axes = [Axis(a.r, a.s, a.method, a.K, w if h else None) for a, w, h in zip(spec["axes"], ws, ctx.has[2:])]
+        need_w = [h and ctx.needs_input_grad[4 + i] for i, h in enumerate(ctx.has[2:])]
+        gx, gmix, gbias, gws = resize_fused_backward(
+            x, gy.to(spec.get("out_dtype") or x.dtype), axes, mix, bias, spec["act"], spec["alpha"], spec["lo"],
+            spec["hi"], spec["pad"], spec["pad_value"], need_dx=ctx.needs_input_grad[0],
+            need_dmix=mix is not None and ctx.needs_input_grad[2],
+            need_dbias=bias is not None and ctx.needs_input_grad[3], need_dw=need_w)
+        return (gx, None, gmix, gbias, *gws)
+
+
+class FCFSFused(torch.nn.Module):
+    """FCFS followed by a 1x1 convolution, bias and activation in one layer (the resize as a
+    layer of a fully convolutional network), trained through FusedFunction."""
+
+    def __init__(self, channels: int, out_channels: int, ratios, method: int = BILINEAR, act: int = ACT_RELU,
+                 alpha: float = 0.0, lo: float = 0.0, hi: float = 0.0, pad: int = PAD_REPLICATE,
+                 pad_value: float = 0.0, learnable: bool = False, K: int = 0, bias: bool = True, out_dtype=None):
+        super().__init__()
+        self.ratios = [tuple(rs) for rs in ratios]
+        self.method, self.act, self.alpha, self.lo, self.hi = method, act, alpha, lo, hi
+        self.pad, self.pad_value, self.out_dtype = pad, pad_value, out_dtype
+        self.mix = torch.nn.Parameter(torch.randn(out_channels, channels) / math.sqrt(channels))
+        self.bias = torch.nn.Parameter(torch.zeros(out_channels)) if bias else None
+        self.weights = torch.nn.ParameterList()
+        self.Ks = []
+        for r, s in self.ratios:
+            w, k = fcfs_make_weights(method, r, s, K)
+            self.Ks.append(k)
+            if learnable:
+                self.weights.append(torch.nn.Parameter(torch.from_numpy(np.tile(w[None], (channels, 1, 1)))))
+        self.learnable = learnable
+
+    def forward(self, x):
+        spec = {"axes": [Axis(r, s, self.method, k) for (r, s), k in zip(self.ratios, self.Ks)],
+                "act": self.act, "alpha": self.alpha, "lo": self.lo, "hi": self.hi, "pad": self.pad,
+                "pad_value": self.pad_value, "out_dtype": self.out_dtype}
+        ws = [w.contiguous() for w in self.weights] if self.learnable else [None] * len(self.ratios)
+        return FusedFunction.apply(x, spec, self.mix.contiguous(), self.bias, *ws)
 
 
 # ------------------------------------------------- non-separable 2D kernels

@@ -160,3 +160,24 @@ def test_reproducible_and_rejections(F):
     with pytest.raises(F.FCFSError):  # a mix gradient for a layer without a mix
         F.fcfs_backward_fused(d, e2, x.data_ptr(), torch.zeros(2, 4, 64, 96, device="cuda").data_ptr(),
                               gx.data_ptr(), mix.data_ptr(), None, None, ws.data_ptr(), need)
+
+
+def test_module_autograd(F, orc):
+    # FCFSFused trained through autograd: every parameter's gradient against the oracle
+    torch.manual_seed(0)
+    layer = F.FCFSFused(3, 4, [(2, 1), (3, 2)], BILINEAR, act=2, alpha=0.1, learnable=True).cuda()
+    with torch.no_grad():
+        layer.bias.copy_(torch.tensor([0.1, -0.2, 0.3, 0.05]))
+        for w in layer.weights:
+            w.add_(0.05 * torch.randn_like(w))
+    x = torch.randn(2, 3, 14, 18, device="cuda", requires_grad=True)
+    y = layer(x)
+    gy = torch.randn_like(y)
+    (y * gy).sum().backward()
+    oaxes = [dict(r=r, s=s, K=k, w=w.detach().double().cpu().numpy())
+             for (r, s), k, w in zip(layer.ratios, layer.Ks, layer.weights)]
+    want = orc.resize_fused_backward(_np(x.detach()), _np(gy), oaxes, _np(layer.mix.detach()),
+                                     _np(layer.bias.detach()), 2, 0.1)
+    for got, w in ((x.grad, want[0]), (layer.mix.grad, want[1]), (layer.bias.grad, want[2]),
+                   (layer.weights[0].grad, want[3][0]), (layer.weights[1].grad, want[3][1])):
+        assert np.abs(_np(got) - w).max() <= 1e-4 * max(1.0, np.abs(w).max())
