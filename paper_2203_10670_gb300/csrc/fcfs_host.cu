@@ -921,7 +921,7 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
     // the x pass reads the span rounded up to VW samples (at least a pair) from each window start
     const int vp = std::max(T->rs_vw, 2);
     const int spanx = rs_ok ? (T->rs_span + vp - 1) / vp * vp : 0;
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < 24; ++it) {
         // capacities over every tile position of each axis
         int vx = 1, vy = 1, gw = 1, gh = 1, wa = 1, fxp = 1;
         for (int q0 = 0; q0 < Nx; q0 += T->QX) {
@@ -961,6 +961,7 @@ static int plan_dx_tma(const fcfs_desc* d, const BwdParams& B, const void* gy, v
         const size_t budget = rs_ok ? 110 * 1024 : 56 * 1024;
         if (T->GBW <= 256 && T->GBH <= 256 && T->bar_off + 8 * T->stages <= budget) break;
         if (T->QX > 64 && T->QX >= 4 * T->QY) T->QX /= 2;
+        else if (rs_ok && T->QY > 32) T->QY -= 8;  // tall tiles shrink in steps of 8 rows to the budget
         else if (T->QY > 8) T->QY /= 2;
         else if (T->QX > 32) T->QX /= 2;
         else break;
