@@ -1484,7 +1484,8 @@ TileChoice default_tma_tiles(const FwdParams& P0, int es, bool is3d) {
     while (wx8 > 1 && (wx8 * rx) % 8) --wx8;
     if ((wx8 * rx) % 8 == 0 && 4 * wx8 >= 3 * WX) WX = wx8;
     if ((WX * rx) % 2 && WX > 1) WX -= 1;
-    int WY = std::max(1, 64 / ry);
+    // two-byte inputs: twice the rows in the same staging bytes (shrunk below when the budget says so)
+    int WY = std::max(1, (es <= 2 ? 128 : 64) / ry);
     for (int it = 0; it < 64; ++it) {
         apply_tiles(P, false, WX, WY, 1, 0);
         int BW, BH, bb, bo;

@@ -48,7 +48,7 @@ extern "C" int fcfs_tune_forward(const fcfs_desc* d, const void* x, void* y, voi
     }
     cands.push_back(def);
     const int ox_targets[] = {64, 128, 192, 256};
-    const int oy_targets[] = {8, 16, 32, 48, 64};
+    const int oy_targets[] = {8, 16, 32, 48, 64, 96, 128};
     const int ry = P0.ax[1].r;
     // 3D: depth windows per tile as well (half, same, double the default)
     const int wd_scale[] = {2, 4, 8};
