@@ -118,7 +118,9 @@ __device__ __forceinline__ void f2_load_tile_split(float* dst, int pitch, int KW
 
 // ------------------------------------------------------------------ forward
 
-template <int NPH, typename Tin, typename Tout>
+// CT, CS > 0: a compile-time tap count on both axes and x stride (the common shapes), so the tap loops
+// unroll and the split-row offsets of the taps fold into constants; 0: read from the parameters.
+template <int NPH, typename Tin, typename Tout, int CT = 0, int CS = 0>
 __global__ void __launch_bounds__(256) fcfs_full2d_fwd(const __grid_constant__ F2Params p) {
     extern __shared__ float4 f2_smem4[];
     float* sW = reinterpret_cast<float*>(f2_smem4);
@@ -130,9 +132,10 @@ __global__ void __launch_bounds__(256) fcfs_full2d_fwd(const __grid_constant__ F
     const int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
     const int c = (int)(plane % p.C);
     const int iy0 = ty * p.WY, ix0 = tx * p.WX;
-    const int TT = AY.T * AX.T, TX = AX.T, Ppad = p.Ppad;
-    const int rows = (p.WY - 1) * AY.s + AY.T, cols = (p.WX - 1) * AX.s + AX.T;
-    const int KW = (cols + AX.s - 1) / AX.s, pitch = KW * AX.s;
+    const int TX = CT ? CT : AX.T, TY = CT ? CT : AY.T, SX = CS ? CS : AX.s;
+    const int TT = TY * TX, Ppad = p.Ppad;
+    const int rows = (p.WY - 1) * AY.s + TY, cols = (p.WX - 1) * SX + TX;
+    const int KW = (cols + SX - 1) / SX, pitch = KW * SX;
     float* sIn = sW + TT * Ppad;
 
     f2_stage_weights(sW, p, c);
@@ -154,10 +157,12 @@ __global__ void __launch_bounds__(256) fcfs_full2d_fwd(const __grid_constant__ F
         for (int k = 0; k < NPH; ++k) a[k] = b[k] = 0.f;
         const float* src = sIn + iyl * AY.s * pitch + ixl;
         const float* wp = sW + ch * NPH;
-        for (int my = 0; my < AY.T; ++my) {
+#pragma unroll
+        for (int my = 0; my < TY; ++my) {
             // tap mx sits at (mx mod s) * KW + mx / s of the split row
             int off = 0, u = 0;
             const float* wq = wp;
+#pragma unroll
             for (int mx = 0; mx < TX; ++mx) {
                 const float v0 = src[off], v1 = src[off + 32];
                 float w[NPH];
@@ -175,9 +180,9 @@ __global__ void __launch_bounds__(256) fcfs_full2d_fwd(const __grid_constant__ F
                 }
                 wq += Ppad;
                 off += KW;
-                if (++u == AX.s) {
+                if (++u == SX) {
                     u = 0;
-                    off += 1 - AX.s * KW;
+                    off += 1 - SX * KW;
                 }
             }
             src += pitch;
@@ -664,7 +669,15 @@ int full2d_forward(const fcfs_desc* d, const void* x, void* y, cudaStream_t st) 
     p.y = y;
     const size_t smem = f2_fwd_smem(p);
     cudaError_t e = cudaErrorInvalidValue;
-#define F2_FWD(NPH, TI, TO) e = f2_launch(fcfs_full2d_fwd<NPH, TI, TO>, p, blocks, smem, st)
+    // compile-time tap counts for the common square windows (T x T taps, x stride s)
+    const int cts = p.ax[0].T == p.ax[1].T ? p.ax[1].T * 16 + p.ax[1].s : 0;
+#define F2_FWD(NPH, TI, TO)                                                                          \
+    do {                                                                                             \
+        if (cts == 5 * 16 + 4) e = f2_launch(fcfs_full2d_fwd<NPH, TI, TO, 5, 4>, p, blocks, smem, st); \
+        else if (cts == 5 * 16 + 1) e = f2_launch(fcfs_full2d_fwd<NPH, TI, TO, 5, 1>, p, blocks, smem, st); \
+        else if (cts == 3 * 16 + 1) e = f2_launch(fcfs_full2d_fwd<NPH, TI, TO, 3, 1>, p, blocks, smem, st); \
+        else e = f2_launch(fcfs_full2d_fwd<NPH, TI, TO>, p, blocks, smem, st);                         \
+    } while (0)
 #define F2_FWD_OUT(NPH, TI)                      \
     if (d->dtype_out == FCFS_F32) F2_FWD(NPH, TI, float); \
     else F2_FWD(NPH, TI, __nv_bfloat16)

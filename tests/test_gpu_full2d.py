@@ -212,3 +212,11 @@ def test_rejections(F):
     d.axis[0].w = w.data_ptr()  # per-axis weights and w2d together
     with pytest.raises(FCFSError):
         F.fcfs_forward(d, x.data_ptr(), x.data_ptr())
+
+
+@pytest.mark.parametrize("pad", (REPL, REFL))
+def test_forward_square_windows_compiled_taps(F, orc, pad):
+    # the shapes with compile-time tap loops: 5 x 5 taps at x stride 4 (the 5/4 layer), 5 x 5 and 3 x 3 at stride 1
+    check_forward(F, orc, (2, 3, 37, 71), ((5, 4), (5, 4)), (2, 2), pad, seed=9)
+    check_forward(F, orc, (1, 2, 29, 43), ((2, 1), (3, 1)), (2, 2), pad, din=torch.bfloat16, dout=torch.bfloat16, seed=10)
+    check_forward(F, orc, (1, 2, 29, 43), ((2, 1), (2, 1)), (1, 1), pad, seed=11)
