@@ -263,3 +263,39 @@ def test_binding_argument_checks_for_the_new_layers():
         fcfs.make_desc_full2d((1, 3, 8, 8, 8), ax + [fcfs.Axis(2, 1, 1)], torch.zeros(2, 2, 3, 3), 0, 0)
     with pytest.raises(ValueError):  # the mix must live on the device
         fcfs.resize_fused(x, ax, mix=torch.zeros(4, 3))
+
+
+def test_fused_backward_host_checks(native):
+    """fcfs_backward_fused_workspace and the argument checks of fcfs_backward_fused: every case here is
+    decided on the host before any device work (the pointers are never dereferenced)."""
+    from paper_2203_10670_gb300 import fcfs
+
+    lib = native.load()
+    d = fcfs.make_desc((2, 3, 16, 20), [fcfs.Axis(2, 1, 1)] * 2, native.FCFS_F32, native.FCFS_F32)
+
+    def epi(**kw):
+        e = native.fcfs_epilogue()
+        e.c_out, e.mix, e.bias, e.act = 5, BOGUS, BOGUS, native.FCFS_ACT_RELU
+        for k, v in kw.items():
+            setattr(e, k, v)
+        return e
+
+    e = epi()
+    need = lib.fcfs_backward_fused_workspace(ctypes.byref(d), ctypes.byref(e))
+    # the recomputed outputs (3 channels) and the activation gradient (5), FP32 at 32 x 40 pixels, at least
+    assert need >= 2 * 32 * 40 * (3 + 5) * 4
+    assert lib.fcfs_backward_fused_workspace(ctypes.byref(d), ctypes.byref(epi(c_out=0))) == 0
+    assert lib.fcfs_backward_fused_workspace(ctypes.byref(d), ctypes.byref(epi(mix=None))) == 0  # 5 != 3
+    d8 = fcfs.make_desc((2, 3, 16, 20), [fcfs.Axis(2, 1, 1)] * 2, native.FCFS_U8, native.FCFS_F32)
+    assert lib.fcfs_backward_fused_workspace(ctypes.byref(d8), ctypes.byref(e)) == 0
+
+    def run(e, gx=BOGUS, gmix=None, gbias=None, ws=BOGUS, nbytes=need):
+        return lib.fcfs_backward_fused(ctypes.byref(d), ctypes.byref(e), BOGUS, BOGUS, gx, gmix, gbias, None, ws,
+                                       nbytes, None)
+
+    assert run(e, ws=None) == native.FCFS_ERR_ARG
+    assert run(e, nbytes=need - 1) == native.FCFS_ERR_ARG
+    assert run(e, ws=BOGUS + 16) == native.FCFS_ERR_ARG  # workspace not 256-byte aligned
+    assert run(epi(mix=None, c_out=3), gmix=BOGUS) == native.FCFS_ERR_ARG  # no mix, no mix gradient
+    assert run(epi(bias=None), gbias=BOGUS) == native.FCFS_ERR_ARG
+    assert run(e, gx=None) == native.FCFS_OK  # nothing asked for: nothing enqueued
